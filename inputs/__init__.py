@@ -1,0 +1,175 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds none of the method's arithmetic: it reads the scalar
+constants that ``oracle/write_scenarios.py`` stored in ``scenarios.json``
+(lattice-unit EOS parameters, relaxation time, reference and Rankine-Hugoniot
+states) and lays them out in space with geometry only (steps, tanh
+interfaces, sines) plus seeded noise.  A ``Case`` is everything one run needs:
+lattice, interior size, EOS dict, tau, Pr, c_v, x boundary specs and the
+initial primitive fields rho, u, T in lattice units.
+
+Array order of every field is ([z,] y, x): x is the fastest (last) axis, the
+same node order x + Nx (y + Ny z) as the C interface.
+
+Random numbers come from SplitMix64 used as a counter-based generator: value
+k of stream ``seed`` is mix(seed + (k + 1) * 0x9E3779B97F4A7C15), with the
+published SplitMix64 finaliser, mapped to [-1, 1) through its top 53 bits.
+"""
+from dataclasses import dataclass, field
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed, n):
+    """n outputs of SplitMix64 started at state ``seed`` (uint64 array)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + k * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed, n):
+    """n values uniform in [-1, 1) from ``splitmix64(seed, n)``."""
+    z = splitmix64(seed, n) >> np.uint64(11)
+    return z.astype(np.float64) * (2.0 ** -52) - 1.0
+
+
+def scenarios():
+    with open(os.path.join(_HERE, "scenarios.json")) as fh:
+        return json.load(fh)
+
+
+def scenario(name):
+    return scenarios()[name]
+
+
+@dataclass
+class Case:
+    """One run: lattice, size, parameters, boundaries and initial fields."""
+    name: str
+    D: int
+    shape: tuple                 # interior (Nx, Ny[, Nz])
+    eos: dict
+    tau: float
+    Pr: float
+    cv: float
+    x_low: object = "periodic"   # "periodic" | "outflow" | ("inflow", (rho, u, T))
+    x_high: object = "periodic"
+    rho: np.ndarray = None
+    u: list = field(default_factory=list)
+    T: np.ndarray = None
+
+    @property
+    def lattice(self):
+        return 9 if self.D == 2 else 27
+
+    @property
+    def nodes(self):
+        return int(np.prod(self.shape))
+
+    def grid(self):
+        """Integer coordinate arrays (x, y[, z]) in array order ([z,] y, x)."""
+        axes = [np.arange(n, dtype=np.float64) for n in self.shape]
+        mesh = np.meshgrid(*reversed(axes), indexing="ij")
+        return list(reversed(mesh))
+
+
+def _base(name, sc, shape, **kw):
+    return Case(name=name, D=sc["D"], shape=tuple(shape), eos=dict(sc["eos"]),
+                tau=sc["tau"], Pr=sc["Pr"], cv=sc["cv"], **kw)
+
+
+def riemann(Nx=1000, Ny=4, split=None):
+    """D2Q9 Riemann problem: left state for x < split, right state beyond.
+
+    x faces are zero-gradient outflow, y is periodic; u = 0.
+    """
+    sc = scenario("riemann_d2q9")
+    split = Nx // 2 if split is None else split
+    c = _base("riemann_d2q9", sc, (Nx, Ny), x_low="outflow", x_high="outflow")
+    x = c.grid()[0]
+    left = x < split
+    c.rho = np.where(left, sc["left"]["rho"], sc["right"]["rho"])
+    c.T = np.where(left, sc["left"]["T"], sc["right"]["T"])
+    c.u = [np.zeros_like(c.rho) for _ in range(2)]
+    return c
+
+
+def _drop_profile(r, R, width):
+    """1 inside the drop, 0 outside, tanh interface of the given width (nodes)."""
+    return 0.5 * (1.0 - np.tanh(2.0 * (r - R) / width))
+
+
+def shock_drop(D=2, shape=(4096, 2048), radius=128, center=None, shock_x=512,
+               width=3.0, with_drop=True, sc=None):
+    """Planar shock hitting a liquid-like drop (2D circle / 3D sphere).
+
+    Vapour at rest everywhere; a drop (pressure-matched temperature) with a
+    tanh interface; for x < shock_x the Rankine-Hugoniot post-shock state
+    moving in +x, which is also the equilibrium inflow at the x = 0 face;
+    the x = Nx - 1 face is zero-gradient outflow; y (and z) periodic.
+    """
+    name = "shock_drop_d2q9" if D == 2 else "shock_drop_d3q27"
+    sc = scenario(name) if sc is None else sc
+    post = sc["post"]
+    u_in = [post["u"]] + [0.0] * (D - 1)
+    c = _base(name, sc, shape, x_low=("inflow", (post["rho"], u_in, post["T"])),
+              x_high="outflow")
+    g = c.grid()
+    if center is None:
+        center = [shape[0] // 4] + [n // 2 for n in shape[1:]]
+    vap, drop = sc["vapour"], sc["drop"]
+    if with_drop:
+        r = np.sqrt(sum((g[a] - center[a]) ** 2 for a in range(D)))
+        s = _drop_profile(r, radius, width)
+    else:
+        s = np.zeros_like(g[0])
+    rho = vap["rho"] + (drop["rho"] - vap["rho"]) * s
+    T = vap["T"] + (drop["T"] - vap["T"]) * s
+    behind = g[0] < shock_x
+    c.rho = np.where(behind, post["rho"], rho)
+    c.T = np.where(behind, post["T"], T)
+    c.u = [np.where(behind, post["u"], 0.0)] + [np.zeros_like(rho) for _ in range(D - 1)]
+    return c
+
+
+def tgv(N=256, shape=None):
+    """D3Q27 periodic Taylor-Green vortex at constant density.
+
+    u = U0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0), k = 2 pi / N per
+    axis; T = T0 + T_amp (cos 2kx + cos 2ky)(cos 2kz + 2), the temperature that
+    gives the classical TGV pressure at constant density (T_amp stored).
+    """
+    sc = scenario("tgv_d3q27")
+    shape = (N, N, N) if shape is None else tuple(shape)
+    c = _base("tgv_d3q27", sc, shape)
+    x, y, z = c.grid()
+    kx, ky, kz = (2 * np.pi / n for n in shape)
+    U0 = sc["U0"]
+    c.rho = np.full(x.shape, sc["rho0"])
+    c.u = [U0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z),
+           -U0 * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z),
+           np.zeros_like(x)]
+    c.T = sc["T0"] + sc["T_amp"] * (np.cos(2 * kx * x) + np.cos(2 * ky * y)) * (np.cos(2 * kz * z) + 2.0)
+    return c
+
+
+def add_noise(c, seed, rel=1e-3):
+    """Seeded perturbation: rho *= 1 + rel U, u += rel c_ref U (U in [-1,1)).
+
+    c_ref is the stored reference sound speed of the scenario.  Streams:
+    seed for rho, seed + 1 + a for u_a.
+    """
+    cs = scenario(c.name)["cs_ref"]
+    n = c.rho.size
+    c.rho = c.rho * (1.0 + rel * uniform(seed, n).reshape(c.rho.shape))
+    c.u = [ua + rel * cs * uniform(seed + 1 + a, n).reshape(ua.shape) for a, ua in enumerate(c.u)]
+    return c

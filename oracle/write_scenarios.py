@@ -1,0 +1,111 @@
+"""Write inputs/scenarios.json: the scalar constants of every benchmark workload.
+
+Run as ``python -m oracle.write_scenarios`` from the repository root.  It calls
+only the oracle's thermodynamics (vdW EOS, sound speed, Rankine-Hugoniot), so
+every stored number is an oracle output, never a CUDA-path output.  The field
+builders in ``inputs/`` read these scalars and add geometry only.
+
+Units.  The workloads are stated in reduced van der Waals units (rho_c = T_c =
+P_c = 1, so R = 8/3, a = 3, b = 1/3; c_v/R = 3).  The lattice scheme is stable
+only for theta = P/rho < 1/3 (Sec. 5), so velocities are rescaled by U: lattice
+u = u_r / U, T = T_r / U^2, a = a_r / U^2, with rho, b, R, c_v unchanged.  U^2 is
+the smallest integer with max(theta_r)/U^2 <= 1/4 over the states of the
+workload.  Viscosities nu are lattice values; mu = nu rho_ref and the stored
+relaxation time is tau = mu / P(rho_ref, T_ref) (Sec. 3.1, tau = mu/P).
+"""
+import json
+import math
+import os
+
+from . import thermo
+
+A_R, B, R_GAS = 3.0, 1.0 / 3.0, 8.0 / 3.0
+CV = 3.0 * R_GAS
+
+
+def _theta_r(rho, T):
+    return thermo.pressure(rho, T, A_R, B, R_GAS) / rho
+
+
+def _u2_for(states):
+    return float(math.ceil(max(_theta_r(r, t) for r, t in states) / 0.25))
+
+
+def _lattice_eos(U2, kappa, eta_over_mu, rho_ref, T_ref_r):
+    return dict(a=A_R / U2, b=B, R=R_GAS, kappa=kappa, eta_over_mu=eta_over_mu,
+                rho_ref=rho_ref, T_ref=T_ref_r / U2)
+
+
+def _tau(eos, nu):
+    P = thermo.pressure(eos["rho_ref"], eos["T_ref"], eos["a"], eos["b"], eos["R"])
+    return nu * eos["rho_ref"] / P
+
+
+def _cs_lattice(rho, T_lat, eos):
+    return math.sqrt(thermo.sound_speed_sq(rho, T_lat, eos["a"], eos["b"], eos["R"], CV))
+
+
+def riemann():
+    """D2Q9 non-ideal Riemann problem (left rho=1.0 T=1.2 | right rho=0.3 T=1.1)."""
+    left, right = (1.0, 1.2), (0.3, 1.1)
+    U2 = _u2_for([left, right])
+    eos = _lattice_eos(U2, kappa=0.01, eta_over_mu=1.0, rho_ref=0.65, T_ref_r=1.15)
+    return dict(D=2, U2=U2, cv=CV, Pr=0.71, nu=0.01, eos=eos, tau=_tau(eos, 0.01),
+                left=dict(rho=left[0], T=left[1] / U2), right=dict(rho=right[0], T=right[1] / U2))
+
+
+def _shock_drop(D, Ma, nu):
+    vap = (0.3, 1.1)
+    rho_d = 1.8
+    P_v = thermo.pressure(vap[0], vap[1], A_R, B, R_GAS)
+    T_d = thermo.temperature_from_pressure(rho_d, P_v, A_R, B, R_GAS)   # pressure match
+    r2, T2, u2, us = thermo.rankine_hugoniot(vap[0], vap[1], 0.0, Ma, A_R, B, R_GAS, CV)
+    U2 = _u2_for([vap, (rho_d, T_d), (r2, T2)])
+    U = math.sqrt(U2)
+    eos = _lattice_eos(U2, kappa=0.01, eta_over_mu=1.0, rho_ref=vap[0], T_ref_r=vap[1])
+    return dict(D=D, U2=U2, cv=CV, Pr=0.71, nu=nu, eos=eos, tau=_tau(eos, nu), Ma=Ma,
+                vapour=dict(rho=vap[0], T=vap[1] / U2),
+                drop=dict(rho=rho_d, T=T_d / U2),
+                post=dict(rho=r2, T=T2 / U2, u=u2 / U),
+                shock_speed=us / U)
+
+
+def tgv():
+    """D3Q27 compressible Taylor-Green vortex in dense vapour (rho0=0.6, T0=1.05, Ma 0.5)."""
+    rho0, T0 = 0.6, 1.05
+    U2 = _u2_for([(rho0, T0)])
+    eos = _lattice_eos(U2, kappa=0.01, eta_over_mu=1.0, rho_ref=rho0, T_ref_r=T0)
+    cs = _cs_lattice(rho0, T0 / U2, eos)
+    U0 = 0.5 * cs
+    # T from Eq. Pvdw at constant rho0 is affine in P:
+    #   T = T0 + dP (1 - b rho0)/(rho0 R),  dP = rho0 U0^2/16 (cos2x + cos2y)(cos2z + 2)
+    T_amp = U0 * U0 * (1.0 - B * rho0) / (16.0 * R_GAS)
+    return dict(D=3, U2=U2, cv=CV, Pr=0.71, nu=1e-3, eos=eos, tau=_tau(eos, 1e-3),
+                rho0=rho0, T0=T0 / U2, U0=U0, T_amp=T_amp, cs=cs)
+
+
+def main():
+    out = dict(
+        riemann_d2q9=riemann(),
+        shock_drop_d2q9=_shock_drop(2, 1.47, 0.01),
+        tgv_d3q27=tgv(),
+        shock_drop_d3q27=_shock_drop(3, 1.47, 0.01),
+    )
+    # parity cases: smaller noise amplitude reference sound speed per scenario
+    for k, sc in out.items():
+        if "vapour" in sc:
+            sc["cs_ref"] = _cs_lattice(sc["vapour"]["rho"], sc["vapour"]["T"], sc["eos"])
+        elif "left" in sc:
+            sc["cs_ref"] = _cs_lattice(sc["right"]["rho"], sc["right"]["T"], sc["eos"])
+        else:
+            sc["cs_ref"] = sc["cs"]
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "inputs", "scenarios.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    print("wrote", path)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,93 @@
+"""Planted mistakes: each plausible slip in the oracle must break at least one pin.
+
+The mistake is planted in the oracle (monkeypatched on the CPU) and the pin
+that should catch it is asserted to fail.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm
+import physics_cases as pc  # noqa: E402
+import test_oracle_step as st
+
+
+def test_dropping_phi_breaks_galilean_invariance(monkeypatch):
+    monkeypatch.setattr(lbm, "galilean_correction", lambda m, rho, u, theta: [0.0 * rho] * m.D)
+    sig, want = pc.acoustic_decay(Max=0.4)
+    assert abs(sig / want - 1) > 0.03
+
+
+def upwind_dependence(galilean_correction):
+    """Phi at x with u_x > 0 (< 0) must not see Lambda at x + 1 (x - 1) (Sec. 3.2 upwinding)."""
+    m = lbm.Model(2, (9, 1), pc.EOS, tau=0.05, Pr=0.71, cv=pc.CV)
+    rho = np.full((1, 9), pc.RHO0)
+    theta = np.full((1, 9), 0.2)
+    for sign in (1.0, -1.0):
+        u = [np.full((1, 9), 0.1 * sign), np.zeros((1, 9))]
+        base = galilean_correction(m, rho, u, theta)[0][0, 4]
+        u2 = [u[0].copy(), u[1]]
+        u2[0][0, 4 + int(sign)] *= 1.5          # changes Lambda downstream only
+        assert galilean_correction(m, rho, u2, theta)[0][0, 4] == base
+
+
+def test_upwind_pin_holds():
+    upwind_dependence(lbm.galilean_correction)
+
+
+def test_flipping_upwind_direction_is_caught(monkeypatch):
+    def downwind(m, rho, u, theta):
+        Phi = []
+        for a in range(m.D):
+            Lam = rho * u[a] ** 3 + 3.0 * rho * u[a] * (theta - lbm.CS2)
+            back, fwd = Lam - m.nb(Lam, a, -1), m.nb(Lam, a, 1) - Lam
+            sgn = -np.sign(u[a])
+            Phi.append(-(0.5 * (1 + sgn) * back + 0.5 * (1 - sgn) * fwd) / rho)
+        return Phi
+    with pytest.raises(AssertionError):
+        upwind_dependence(downwind)
+
+
+def test_dropping_heat_flux_correction_breaks_thermal_pin(monkeypatch):
+    monkeypatch.setattr(lbm, "heat_flux_correction", lambda P, gh, gT, k: [0.0 * P for _ in gh])
+    chi, want = pc.thermal_decay()
+    assert abs(chi / want - 1) > 0.03
+
+
+def test_alpha_zero_breaks_acoustic_pin(monkeypatch):
+    monkeypatch.setattr(lbm, "bulk_shift", lambda D, rho, cs2, P, e: 0.0 * rho)
+    sig, want = pc.acoustic_decay()
+    assert abs(sig / want - 1) > 0.03
+
+
+def test_sign_of_eta_term_breaks_acoustic_pin(monkeypatch):
+    monkeypatch.setattr(lbm, "bulk_shift", lambda D, rho, cs2, P, e: (D + 2.0) / D - rho * cs2 / P + e)
+    sig, want = pc.acoustic_decay()
+    assert abs(sig / want - 1) > 0.03
+
+
+def test_dropping_energy_compensation_breaks_identity(monkeypatch):
+    monkeypatch.setattr(lbm, "shifted_temperature", lambda T, F, rho, cv: T)
+    with pytest.raises(AssertionError):
+        st.test_moment_identities_with_korteweg(2, (12, 9))
+
+
+def test_dropping_half_force_in_velocity_breaks_identity(monkeypatch):
+    monkeypatch.setattr(lbm, "velocity", lambda j, F, rho: [j[a] / rho for a in range(len(j))])
+    with pytest.raises(AssertionError):
+        st.test_moment_identities_with_korteweg(2, (12, 9))
+
+
+def test_transposed_chi_breaks_geq_moments(monkeypatch):
+    orig = lbm.chi
+    monkeypatch.setattr(lbm, "chi", lambda c, u, theta: orig(-c, u, theta))
+    import test_oracle_equilibria as te
+    with pytest.raises(AssertionError):
+        te.test_geq_moments(3, 0)
+
+
+def test_wrong_psi_rest_factor_breaks_weights(monkeypatch):
+    orig = lbm.psi
+    monkeypatch.setattr(lbm, "psi", lambda c, xi, zeta: 1.0 - 0.5 * zeta if c == 0 else orig(c, xi, zeta))
+    import test_oracle_equilibria as te
+    with pytest.raises(AssertionError):
+        te.test_weights_at_rest(3)
