@@ -1,0 +1,334 @@
+"""Throughput benchmark of the fused non-ideal LBM step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload tgv256|tgv256-fp64|tgv256-fp16dev|riemann|shockdrop2d]
+
+Prints one JSON line (rank 0).  A step is one full time step of the method
+(stream, moments, EOS, correction terms, collide, boundary fill) over the
+whole lattice.  ``value`` is MLUPS (million lattice-node updates per second)
+with the state resident in HBM; ``e2e`` is the same metric through the C
+interface with host buffers: lbm_init from pinned host fields, K calls of
+lbm_step(h, 1) (each reads the 4-byte status word back), lbm_moments to host.
+With N GPUs (torchrun) every rank runs an independent replica of the
+workload (the solver is single-GPU); the value is the sum over ranks of the
+updates divided by the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (the only other place this
+file runs oracle code) on a bounded sample of the workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (builder kwargs, precision, description)
+    "tgv256": ("tgv", dict(N=256), "fp32", "D3Q27 compressible Taylor-Green vortex 256^3, vdW dense vapour, FP32"),
+    "tgv256-fp64": ("tgv", dict(N=256), "fp64", "D3Q27 compressible Taylor-Green vortex 256^3, FP64"),
+    "tgv256-fp16dev": ("tgv", dict(N=256), "fp16dev", "D3Q27 Taylor-Green 256^3, FP16-deviation storage"),
+    "riemann": ("riemann", dict(), "fp64", "D2Q9 non-ideal Riemann problem 1000x4, FP64"),
+    "shockdrop2d": ("shock_drop", dict(D=2, shape=(4096, 2048)), "fp32",
+                    "D2Q9 shock-drop 4096x2048 (Ma 1.47 inflow), FP32"),
+}
+BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16-storage/f32"}
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_fused.cuh", "lbm_capi.cu"]
+
+
+def build_case(name):
+    import inputs
+    builder, kw, prec, desc = WORKLOADS[name]
+    return getattr(inputs, builder)(**kw), prec, desc
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2510_14712_gb300", "csrc")
+    for f in KERNEL_SOURCES:
+        p = os.path.join(src, f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(workload):
+    """ncu DRAM bytes per step from profiles/traffic.json, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_step")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join("/tmp", "lbm_clocks_%d.csv" % os.getpid())
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def cpu_oracle_leg(workload, seconds=15.0, steps=None, warmup=1):
+    """Time the FP64 oracle on a bounded sample of the workload (runs in a child process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import bench, json; print(json.dumps(bench._oracle_sample(%r, %r, %r, %r)))"
+            % (workload, seconds, steps, warmup))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr else "oracle leg failed"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _oracle_sample(workload, seconds, steps=None, warmup=1):
+    """Oracle MLUPS on a sub-box of the workload: same physics, fewer nodes, few steps.
+
+    With ``steps`` given, exactly that many timed steps after ``warmup``;
+    otherwise as many as fit in ``seconds`` (at most 1000).
+    """
+    import numpy as np
+    import inputs
+    from oracle import lbm as olbm
+    builder, kw, prec, _ = WORKLOADS[workload]
+    if builder == "tgv":
+        case = inputs.tgv(shape=(48, 48, 48))
+        sample = "D3Q27 Taylor-Green 48^3 box (same state, k scaled), FP64 oracle"
+    elif builder == "riemann":
+        case = inputs.riemann()
+        sample = "D2Q9 Riemann 1000x4 (the full workload), FP64 oracle"
+    else:
+        case = inputs.shock_drop(2, (512, 256), radius=16, center=(128, 128), shock_x=64)
+        sample = "D2Q9 shock-drop 512x256 down-scale, FP64 oracle"
+    m = olbm.Model(case.D, case.shape, case.eos, case.tau, case.Pr, case.cv, case.x_low, case.x_high)
+    s = olbm.Sim(m, case.rho, case.u, case.T)
+    s.step(warmup)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and (el > seconds or done >= 1000)):
+            break
+    n = int(np.prod(case.shape))
+    return {"value": n * done / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%s, %d steps, %.1f s, 1 thread" % (sample, done, el)}
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores: W warm-up and K timed steps of the bounded sample."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    desc = WORKLOADS[args.workload][3]
+    r = cpu_oracle_leg(args.workload, steps=args.steps, warmup=args.warmup)
+    if "error" in r:
+        print(json.dumps({"impl": "reference", "unavailable": r["error"]}))
+        return 0
+    v = r["value"]
+    line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "impl": "FP64 CPU oracle (numpy), bounded sample"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2510_14712_gb300 import build
+    build.build()
+    import paper_2510_14712_gb300 as P
+
+    case, prec, desc = build_case(args.workload)
+    if args.precision:
+        prec = args.precision
+    N = case.nodes
+    stream = torch.cuda.current_stream(dev)
+    solver = P.Solver(case, precision=prec, stream=stream.cuda_stream)
+    rho = torch.from_numpy(np.ascontiguousarray(case.rho, dtype=np.float64)).to(dev)
+    u = torch.from_numpy(np.ascontiguousarray(np.stack(case.u), dtype=np.float64)).to(dev)
+    T = torch.from_numpy(np.ascontiguousarray(case.T, dtype=np.float64)).to(dev)
+    P.lbm_init_device(solver.h, rho, u, T)
+
+    # warm-up
+    P.lbm_step(solver.h, args.warmup)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+
+    # timed region: device events around every step on the solver's stream
+    cvd = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    phys = cvd[dev.index] if dev.index < len(cvd) and cvd[dev.index].isdigit() else str(dev.index)
+    clocks = ClockSampler(phys)
+    time.sleep(0.4)
+    launches0 = P.lbm_launch_count(solver.h)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    for k in range(args.steps):
+        P.lbm_step_async(solver.h, 1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    P.lbm_sync(solver.h)
+    launches = P.lbm_launch_count(solver.h) - launches0
+    clk = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = N * args.steps * world / (total_ms * 1e-3) / 1e6
+
+    # roofline of the step kernel(s): algorithmic 4 Q s bytes per node update
+    Q = case.lattice
+    alg_bytes = 4 * Q * BYTES[prec] * N
+    avg_step_s = statistics.mean(step_ms) * 1e-3
+    achieved = alg_bytes / avg_step_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profile_traffic(args.workload + ":" + prec)
+    flags = P.lbm_get_flags(solver.h)
+    solver.close()
+
+    # end to end through the C interface with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        h_rho = torch.from_numpy(np.ascontiguousarray(case.rho, dtype=np.float64)).pin_memory()
+        h_u = torch.from_numpy(np.ascontiguousarray(np.stack(case.u), dtype=np.float64)).pin_memory()
+        h_T = torch.from_numpy(np.ascontiguousarray(case.T, dtype=np.float64)).pin_memory()
+        o_rho, o_u, o_T = torch.empty_like(h_rho).pin_memory(), torch.empty_like(h_u).pin_memory(), \
+            torch.empty_like(h_T).pin_memory()
+        tot = np.empty(case.D + 2)
+        s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream)
+        lib = P.load()
+        import ctypes
+        vp = lambda t: ctypes.c_void_p(t.data_ptr())
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        P._check(lib.lbm_init(s2.h, vp(h_rho), vp(h_u), vp(h_T)))
+        for _ in range(args.steps):
+            P._check(lib.lbm_step(s2.h, 1))
+        P._check(lib.lbm_moments(s2.h, vp(o_rho), vp(o_u), vp(o_T), tot.ctypes.data_as(ctypes.c_void_p)))
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        s2.close()
+        fb = N * (case.D + 2) * 8
+        e2e = {"value": N * args.steps * world / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": fb / args.steps,
+               "d2h_bytes_per_step": 4 + (fb + 8 * (case.D + 2)) / args.steps}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+            "config": {"workload": desc, "nodes": N, "lattice": "D%dQ%d" % (case.D, Q), "precision": prec,
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "step (all launches of one time step)",
+                         "algorithmic_bytes_per_step": alg_bytes, "peak_source": peak_kind},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "status_flags": flags,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_oracle_leg(args.workload)
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv256", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp16dev"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * lbm.h - C interface of the GB300 (sm_103a) lattice Boltzmann solver for
+ * non-ideal compressible flow (Hosseini, Feinberg & Karlin, "Lattice
+ * Boltzmann model for non-ideal compressible fluid dynamics").
+ *
+ * One step of the method, at every node (Sec. 3.2 and Fig. FlowChart):
+ * pull-stream the mass-momentum populations f_i and the bulk-energy
+ * populations g_i, take the moments rho, rho u, rho E (Eqs. def_h, def_u,
+ * def_E), evaluate the van der Waals EOS and the explicit temperature
+ * (Eqs. Pvdw, lbm_temp), build the Korteweg force, the Galilean correction
+ * Phi and the heat-flux correction q^c from neighbour moments (Eqs. FK,
+ * correction, qc_1), form the equilibria and shifted equilibria in product
+ * form (Eqs. LBMeq, LBMstar, LBMeqG, LBMgstar) and collide (Eqs. fLBGK,
+ * gLBGK).  Lattices: D2Q9 and D3Q27 (Eq. D3Q27c).  Lattice units:
+ * delta x = delta t = 1.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status (LBM_OK = 0 or a negative LBM_E*).
+ *    No exception or abort crosses this interface.
+ *  - Host arrays are caller-owned; the library copies in or out and keeps
+ *    no pointer to them.  Device memory is owned by the handle.
+ *  - Field arrays hold the Nx*Ny*Nz interior nodes in the order
+ *    n = x + Nx*(y + Ny*z) (x fastest).  Vector fields are D consecutive
+ *    planes of that size (u_x plane, then u_y, then u_z).
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - All GPU work of a handle runs on its stream (lbm_set_stream).
+ *  - Errors are reported, never trapped: a non-finite or non-positive
+ *    density or temperature found during lbm_step sets a sticky device
+ *    error word; lbm_step then returns LBM_EUNSTABLE, keeps the state for
+ *    inspection, and refuses further steps with LBM_ESTATE until lbm_init.
+ *
+ * Boundaries: y and z are periodic.  The two x faces are either both
+ * periodic, or each is an inflow face (post-collision populations of four
+ * ghost layers set to the equilibrium of a prescribed state, every step) or
+ * a zero-gradient outflow face (ghost layers copy the nearest interior
+ * layer).  The paper gives no boundary scheme; this is the library's.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_s* lbm_t;
+
+/* lattices (Eq. D3Q27c; D2Q9 is its two-dimensional product reduction) */
+enum { LBM_D2Q9 = 9, LBM_D3Q27 = 27 };
+
+/* status codes */
+enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,     /* bad argument (size, pointer, parameter range)       */
+  LBM_ENOMEM = -2,     /* device or host allocation failed                    */
+  LBM_ECUDA = -3,      /* a CUDA runtime call failed (message: lbm_last_error)*/
+  LBM_EUNSTABLE = -4,  /* non-finite or non-positive rho / T produced         */
+  LBM_ESTATE = -5      /* call not valid in the handle's state                */
+};
+
+/* storage / arithmetic precision of the populations */
+enum {
+  LBM_FP64 = 0,        /* FP64 storage, FP64 arithmetic                       */
+  LBM_FP32 = 1,        /* FP32 storage, FP32 arithmetic                       */
+  LBM_FP16DEV = 2      /* FP16 storage of p_i - p_i^ref, FP32 arithmetic      */
+};
+
+/* thermodynamic closure of the (rho, e) -> (T, P, c_s^2) step */
+enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
+
+/* x-face boundary types */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_OUTFLOW = 1, LBM_BC_INFLOW = 2 };
+
+/* faces for lbm_set_boundary */
+enum { LBM_FACE_XLO = 0, LBM_FACE_XHI = 1 };
+
+/* sticky status bits (lbm_get_flags) */
+enum {
+  LBM_FLAG_NONFINITE = 1u,   /* fatal: rho, u or T not finite                 */
+  LBM_FLAG_NEGATIVE = 2u,    /* fatal: rho <= 0 or T <= 0                      */
+  LBM_FLAG_THETA = 4u,       /* warning: theta = P/rho >= 1/3 (Sec. 5 bound)   */
+  LBM_FLAG_PRESSURE = 8u     /* warning: P <= 0                                */
+};
+
+/* van der Waals fluid and model parameters, lattice units.
+ *   P = rho R T / (1 - b rho) - a rho^2               (Eq. Pvdw)
+ *   e = c_v T - a rho                                 (Eq. de_vdW)
+ * kappa: Korteweg capillarity coefficient, F = kappa rho grad lap rho (Eq. FK).
+ * eta_over_mu: bulk to shear viscosity ratio entering alpha (Eq. corr_bulk).
+ * rho_ref, T_ref: reference state fixing the constant mu = tau P(rho_ref, T_ref)
+ *   and k = mu c_p(rho_ref, T_ref) / Pr; for LBM_FP16DEV also the state whose
+ *   equilibria are subtracted before storage.
+ * kind must be 0 (van der Waals). */
+typedef struct {
+  int kind;
+  double a, b, R;
+  double kappa;
+  double eta_over_mu;
+  double rho_ref, T_ref;
+  int precision;       /* LBM_FP64 | LBM_FP32 | LBM_FP16DEV */
+  int closure;         /* LBM_CLOSURE_EXACT | LBM_CLOSURE_MLP */
+} lbm_eos;
+
+/* Create a solver of Nx*Ny*Nz interior nodes (Nz = 1 for D2Q9).
+ * tau: relaxation time at the reference state; the shear viscosity is the
+ *   constant mu = tau P(rho_ref, T_ref) and the local relaxation time is
+ *   mu / P (Sec. 3.1, tau = mu/P; beta of Eq. beta_main).
+ * Pr: Prandtl number mu c_p / k at the reference state (enters q^c, Eq. qc).
+ * cv: specific heat at constant volume.
+ * Allocates the device state (two population buffers, scratch).  Both x faces
+ * start periodic.  Errors: LBM_EINVAL (out is NULL, lattice not 9/27, a size
+ * < 1, Nz != 1 with D2Q9, a non-positive tau, Pr, cv, b rho_ref >= 1,
+ * unsupported precision/closure), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* eos,
+               double tau, double Pr, double cv);
+
+/* Set the type of one x face before lbm_init.  state (for LBM_BC_INFLOW only)
+ * points to D+2 doubles (rho, u_1..u_D, T) of the inflow state; otherwise
+ * it may be NULL.  Setting one face to LBM_BC_PERIODIC sets both.  Changing
+ * between periodic and non-periodic after lbm_create re-lays out the device
+ * state (the state must then be re-initialised).
+ * Errors: LBM_EINVAL (bad face/type, NULL state for inflow, non-positive
+ * rho or T), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_set_boundary(lbm_t h, int face, int type, const double* state);
+
+/* Use the given cudaStream_t (passed as void*) for all later work of this
+ * handle; NULL selects the legacy default stream.  Errors: LBM_EINVAL. */
+int lbm_set_stream(lbm_t h, void* stream);
+
+/* Initialise every node (ghosts included, extended by the face rules) to the
+ * equilibria f^eq(rho, u, theta), g^eq(rho, u, T, theta) with theta = P/rho
+ * (Fig. FlowChart, "Initialize").  rho, T: Nx*Ny*Nz doubles; u: D planes.
+ * All three are required host arrays.  Clears the sticky error word.
+ * Errors: LBM_EINVAL (NULL pointer), LBM_ECUDA. */
+int lbm_init(lbm_t h, const double* rho, const double* u, const double* T);
+
+/* Same as lbm_init but the three arrays are device pointers (FP64, same
+ * layout) already resident on the handle's device. */
+int lbm_init_device(lbm_t h, const double* d_rho, const double* d_u, const double* d_T);
+
+/* Advance n >= 0 time steps.  Returns after enqueuing the work and reading
+ * the 4-byte sticky error word once (one stream synchronisation).
+ * Errors: LBM_ESTATE (not initialised, or a previous step was unstable),
+ * LBM_EINVAL (n < 0), LBM_EUNSTABLE (fatal flag raised; state kept),
+ * LBM_ECUDA. */
+int lbm_step(lbm_t h, int n);
+
+/* Enqueue n steps without reading the error word (no synchronisation); the
+ * fatal flags are reported by the next lbm_step, lbm_sync or lbm_moments.
+ * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ECUDA. */
+int lbm_step_async(lbm_t h, int n);
+
+/* Wait for the handle's stream and report the sticky error word as
+ * lbm_step does. */
+int lbm_sync(lbm_t h);
+
+/* Macroscopic fields of the current state (Eqs. def_h, def_u, def_E,
+ * lbm_temp): rho (Nx*Ny*Nz), u (D planes), T (Nx*Ny*Nz) as FP64 host arrays,
+ * and totals[D+2] = (sum rho, sum rho u_1..u_D, sum rho E) over the interior
+ * in FP64.  Any pointer may be NULL to skip that output.  Synchronises.
+ * Errors: LBM_ESTATE (not initialised), LBM_ECUDA. */
+int lbm_moments(lbm_t h, double* rho, double* u, double* T, double* totals);
+
+/* Same outputs as lbm_moments into device pointers (FP64, same layout);
+ * totals stays a host pointer.  Any pointer may be NULL. */
+int lbm_moments_device(lbm_t h, double* d_rho, double* d_u, double* d_T, double* totals);
+
+/* Sticky status bits (LBM_FLAG_*) raised since the last lbm_init. */
+int lbm_get_flags(lbm_t h, unsigned* flags);
+
+/* Copy the raw population buffer (the post-collision populations of the
+ * last step, ghosts included, library layout) out to / in from a host buffer
+ * of lbm_population_bytes() bytes; used for checkpoint and resume.  A resumed
+ * run continues bit-identically.  Errors: LBM_EINVAL (size mismatch / NULL),
+ * LBM_ESTATE (get before init), LBM_ECUDA. */
+size_t lbm_population_bytes(lbm_t h);
+int lbm_get_populations(lbm_t h, void* host, size_t bytes);
+int lbm_set_populations(lbm_t h, const void* host, size_t bytes);
+
+/* Kernel launches enqueued by this handle since creation (for accounting). */
+long long lbm_launch_count(lbm_t h);
+
+/* Free all resources of the handle.  lbm_destroy(NULL) is a no-op. */
+int lbm_destroy(lbm_t h);
+
+/* Human-readable description of the last error on this thread. */
+const char* lbm_last_error(void);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,260 @@
+"""Python binding of the GB300 non-ideal compressible LBM library (include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``_build/liblbm.so``.  The functions carry the names of the C
+entry points; ``Solver`` is a small convenience wrapper around one handle.
+Importing this package fails loudly when the library has not been built
+(``python -m paper_2510_14712_gb300.build``); there is no CPU fallback.
+
+Field arrays follow the C convention: interior nodes in the order
+n = x + Nx (y + Ny z); as numpy arrays of shape ([Nz,] Ny, Nx).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+LBM_D2Q9, LBM_D3Q27 = 9, 27
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
+LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
+LBM_CLOSURE_EXACT, LBM_CLOSURE_MLP = 0, 1
+LBM_BC_PERIODIC, LBM_BC_OUTFLOW, LBM_BC_INFLOW = 0, 1, 2
+LBM_FACE_XLO, LBM_FACE_XHI = 0, 1
+LBM_FLAG_NONFINITE, LBM_FLAG_NEGATIVE, LBM_FLAG_THETA, LBM_FLAG_PRESSURE = 1, 2, 4, 8
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
+
+# every symbol include/lbm.h declares (checked by tests/test_abi.py)
+EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
+           "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
+           "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
+           "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+class lbm_eos(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("R", ctypes.c_double), ("kappa", ctypes.c_double), ("eta_over_mu", ctypes.c_double),
+                ("rho_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
+                ("precision", ctypes.c_int), ("closure", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """The loaded shared library (raises ImportError when it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("CUDA library not built (%s missing): run "
+                          "`python -m paper_2510_14712_gb300.build`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "lbm_create": (I, [ctypes.POINTER(P), I, I, I, I, ctypes.POINTER(lbm_eos), D, D, D]),
+        "lbm_set_boundary": (I, [P, I, I, dp]),
+        "lbm_set_stream": (I, [P, P]),
+        "lbm_init": (I, [P, P, P, P]),
+        "lbm_init_device": (I, [P, P, P, P]),
+        "lbm_step": (I, [P, I]),
+        "lbm_step_async": (I, [P, I]),
+        "lbm_sync": (I, [P]),
+        "lbm_moments": (I, [P, P, P, P, P]),
+        "lbm_moments_device": (I, [P, P, P, P, P]),
+        "lbm_get_flags": (I, [P, ctypes.POINTER(ctypes.c_uint)]),
+        "lbm_population_bytes": (S, [P]),
+        "lbm_get_populations": (I, [P, P, S]),
+        "lbm_set_populations": (I, [P, P, S]),
+        "lbm_launch_count": (ctypes.c_longlong, [P]),
+        "lbm_destroy": (I, [P]),
+        "lbm_last_error": (ctypes.c_char_p, []),
+        "lbm_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Host pointer of a C-contiguous float64 numpy array (or None)."""
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dptr(t):
+    """Device pointer of a torch CUDA tensor (float64, contiguous) or None."""
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- entry points (same names as the C interface) ---------------------------
+
+def lbm_create(lattice, Nx, Ny, Nz, eos, tau, Pr, cv, precision="fp64", closure=LBM_CLOSURE_EXACT):
+    lib = load()
+    e = lbm_eos(kind=0, a=eos["a"], b=eos["b"], R=eos["R"], kappa=eos["kappa"],
+                eta_over_mu=eos["eta_over_mu"], rho_ref=eos["rho_ref"], T_ref=eos["T_ref"],
+                precision=PRECISIONS.get(precision, precision), closure=closure)
+    h = ctypes.c_void_p()
+    _check(lib.lbm_create(ctypes.byref(h), lattice, Nx, Ny, Nz, ctypes.byref(e), tau, Pr, cv))
+    return h
+
+
+def lbm_set_boundary(h, face, bctype, state=None):
+    st = None
+    if state is not None:
+        arr = np.ascontiguousarray(state, dtype=np.float64)
+        st = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(load().lbm_set_boundary(h, face, bctype, st))
+
+
+def lbm_set_stream(h, stream_ptr):
+    _check(load().lbm_set_stream(h, ctypes.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def lbm_init(h, rho, u, T):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    _check(load().lbm_init(h, _ptr(rho), _ptr(u), _ptr(T)))
+
+
+def lbm_init_device(h, rho, u, T):
+    _check(load().lbm_init_device(h, _dptr(rho), _dptr(u), _dptr(T)))
+
+
+def lbm_step(h, n):
+    _check(load().lbm_step(h, n))
+
+
+def lbm_step_async(h, n):
+    _check(load().lbm_step_async(h, n))
+
+
+def lbm_sync(h):
+    _check(load().lbm_sync(h))
+
+
+def lbm_moments(h, shape, D, want=("rho", "u", "T", "totals")):
+    """Host outputs as numpy arrays of the given ([Nz,] Ny, Nx) shape."""
+    out = {}
+    rho = np.empty(shape) if "rho" in want else None
+    u = np.empty((D,) + tuple(shape)) if "u" in want else None
+    T = np.empty(shape) if "T" in want else None
+    tot = np.empty(D + 2) if "totals" in want else None
+    _check(load().lbm_moments(h, _ptr(rho), _ptr(u), _ptr(T), _ptr(tot)))
+    for k, v in (("rho", rho), ("u", u), ("T", T), ("totals", tot)):
+        if v is not None:
+            out[k] = v
+    return out
+
+
+def lbm_moments_device(h, rho=None, u=None, T=None, totals=None):
+    _check(load().lbm_moments_device(h, _dptr(rho), _dptr(u), _dptr(T), _ptr(totals)))
+
+
+def lbm_get_flags(h):
+    f = ctypes.c_uint()
+    _check(load().lbm_get_flags(h, ctypes.byref(f)))
+    return f.value
+
+
+def lbm_population_bytes(h):
+    return load().lbm_population_bytes(h)
+
+
+def lbm_get_populations(h):
+    n = lbm_population_bytes(h)
+    buf = np.empty(n, dtype=np.uint8)
+    _check(load().lbm_get_populations(h, buf.ctypes.data_as(ctypes.c_void_p), n))
+    return buf
+
+
+def lbm_set_populations(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load().lbm_set_populations(h, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
+
+
+def lbm_launch_count(h):
+    return load().lbm_launch_count(h)
+
+
+def lbm_destroy(h):
+    if h:
+        load().lbm_destroy(h)
+
+
+def lbm_version():
+    return load().lbm_version().decode()
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+class Solver:
+    """One handle set up from an ``inputs.Case``-like description."""
+
+    def __init__(self, case, precision="fp64", stream=None):
+        self.case = case
+        self.D = case.D
+        Nx, Ny = case.shape[0], case.shape[1]
+        Nz = case.shape[2] if case.D == 3 else 1
+        self.arr_shape = tuple(reversed(case.shape))
+        self.h = lbm_create(case.lattice, Nx, Ny, Nz, case.eos, case.tau, case.Pr, case.cv, precision)
+        if stream:
+            lbm_set_stream(self.h, stream)
+        for face, spec in ((LBM_FACE_XLO, case.x_low), (LBM_FACE_XHI, case.x_high)):
+            if spec == "periodic":
+                continue
+            if spec == "outflow":
+                lbm_set_boundary(self.h, face, LBM_BC_OUTFLOW)
+            else:
+                _, (rb, ub, Tb) = spec
+                lbm_set_boundary(self.h, face, LBM_BC_INFLOW, [rb] + list(ub)[:self.D] + [Tb])
+
+    def init(self, rho=None, u=None, T=None):
+        c = self.case
+        rho = c.rho if rho is None else rho
+        u = c.u if u is None else u
+        T = c.T if T is None else T
+        lbm_init(self.h, np.asarray(rho, dtype=np.float64), np.stack([np.asarray(x, dtype=np.float64) for x in u]),
+                 np.asarray(T, dtype=np.float64))
+        return self
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+        return self
+
+    def fields(self):
+        return lbm_moments(self.h, self.arr_shape, self.D)
+
+    def close(self):
+        lbm_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass

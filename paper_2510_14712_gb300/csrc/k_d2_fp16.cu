@@ -1,0 +1,7 @@
+// Kernel set: D = 2, storage Fp16Dev, arithmetic float.
+#include "lbm_ops.cuh"
+
+namespace lbm {
+const Ops* ops_d2_fp16() { return OpsImpl<2, Fp16Dev, float>::ops(); }
+size_t scratch_bytes_d2_fp16(const Params& p) { return OpsImpl<2, Fp16Dev, float>::scratch_bytes(p); }
+}  // namespace lbm

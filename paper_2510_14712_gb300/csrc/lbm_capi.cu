@@ -1,0 +1,365 @@
+// lbm_capi.cu - the extern "C" interface declared in include/lbm.h.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+size_t scratch_bytes_d2_fp64(const Params&);
+size_t scratch_bytes_d2_fp32(const Params&);
+size_t scratch_bytes_d3_fp64(const Params&);
+size_t scratch_bytes_d3_fp32(const Params&);
+size_t scratch_bytes_d2_fp16(const Params&);
+size_t scratch_bytes_d3_fp16(const Params&);
+}  // namespace lbm
+
+using namespace lbm;
+
+// the opaque handle type of the C interface
+struct lbm_s : public Handle {};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+const Ops* ops_for(const Handle& h) {
+  if (h.D == 2) {
+    if (h.precision == LBM_FP64) return ops_d2_fp64();
+    if (h.precision == LBM_FP32) return ops_d2_fp32();
+    return ops_d2_fp16();
+  }
+  if (h.precision == LBM_FP64) return ops_d3_fp64();
+  if (h.precision == LBM_FP32) return ops_d3_fp32();
+  return ops_d3_fp16();
+}
+
+size_t scratch_for(const Handle& h) {
+  if (h.D == 2) {
+    if (h.precision == LBM_FP64) return scratch_bytes_d2_fp64(h.p);
+    if (h.precision == LBM_FP32) return scratch_bytes_d2_fp32(h.p);
+    return scratch_bytes_d2_fp16(h.p);
+  }
+  if (h.precision == LBM_FP64) return scratch_bytes_d3_fp64(h.p);
+  if (h.precision == LBM_FP32) return scratch_bytes_d3_fp32(h.p);
+  return scratch_bytes_d3_fp16(h.p);
+}
+
+Model<double> host_model(const Handle& h) { return model_of<double>(h.p); }
+
+void free_state(Handle& h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h.pop[k]) cudaFree(h.pop[k]);
+    h.pop[k] = nullptr;
+  }
+  if (h.scratch) cudaFree(h.scratch);
+  h.scratch = nullptr;
+  if (h.io_dev) cudaFree(h.io_dev);
+  h.io_dev = nullptr;
+}
+
+// geometry of the padded layout and the device allocations that depend on it
+int layout(Handle& h) {
+  free_state(h);
+  Params& p = h.p;
+  p.G = p.periodic_x ? 0 : kGhost;
+  const int nxp = p.Nx + 2 * p.G;
+  p.pitch = ((nxp + 31) / 32) * 32;      // rows start on 128-element (>= 256 B) boundaries
+  p.plane = (long long)p.Nz * p.Ny * p.pitch;
+  const size_t pop_bytes = size_t(2 * h.Q) * size_t(p.plane) * h.elem_bytes;
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMalloc(&h.pop[k], pop_bytes));
+    CK(cudaMemsetAsync(h.pop[k], 0, pop_bytes, h.stream));
+  }
+  h.scratch_bytes = scratch_for(h);
+  CK(cudaMalloc(&h.scratch, h.scratch_bytes));
+  h.io_bytes = size_t(h.D + 2) * size_t(h.Nx) * h.Ny * h.Nz * sizeof(double);
+  CK(cudaMalloc(&h.io_dev, h.io_bytes));
+  h.cur = 0;
+  h.initialized = 0;
+  return LBM_OK;
+}
+
+void set_face_eq(Handle& h, int face) {
+  Params& p = h.p;
+  const double* st = face == 0 ? p.st_lo : p.st_hi;
+  double* eq = face == 0 ? p.eq_lo : p.eq_hi;
+  Model<double> m = host_model(h);
+  double feq[27], geq[27], u[3] = {st[1], st[2], st[3]};
+  if (h.D == 2) equilibria<2, double>(m, st[0], u, st[4], feq, geq);
+  else equilibria<3, double>(m, st[0], u, st[4], feq, geq);
+  for (int i = 0; i < h.Q; ++i) {
+    eq[i] = feq[i];
+    eq[h.Q + i] = geq[i];
+  }
+}
+
+int read_err(Handle& h) {
+  CK(cudaMemcpyAsync(h.err_host, h.err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  if (*h.err_host & (LBM_FLAG_NONFINITE | LBM_FLAG_NEGATIVE)) {
+    h.unstable = 1;
+    return fail(LBM_EUNSTABLE, "non-finite or non-positive density/temperature produced");
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+const char* lbm_version(void) { return "gb300-nonideal-lbm 0.1"; }
+
+int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* eos, double tau, double Pr,
+               double cv) {
+  if (!out || !eos) return fail(LBM_EINVAL, "out and eos must be non-NULL");
+  *out = nullptr;
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return fail(LBM_EINVAL, "lattice must be 9 or 27");
+  const int D = lattice == LBM_D2Q9 ? 2 : 3;
+  if (Nx < 1 || Ny < 1 || Nz < 1) return fail(LBM_EINVAL, "sizes must be >= 1");
+  if (D == 2 && Nz != 1) return fail(LBM_EINVAL, "D2Q9 needs Nz == 1");
+  if (!(tau > 0) || !(Pr > 0) || !(cv > 0)) return fail(LBM_EINVAL, "tau, Pr, cv must be > 0");
+  if (eos->kind != 0) return fail(LBM_EINVAL, "only the van der Waals EOS (kind 0) is supported");
+  if (!(eos->rho_ref > 0) || !(eos->T_ref > 0) || !(eos->b * eos->rho_ref < 1) || !(eos->R > 0))
+    return fail(LBM_EINVAL, "need rho_ref > 0, T_ref > 0, R > 0, b rho_ref < 1");
+  if (eos->precision < LBM_FP64 || eos->precision > LBM_FP16DEV) return fail(LBM_EINVAL, "bad precision");
+  if (eos->closure != LBM_CLOSURE_EXACT) return fail(LBM_EINVAL, "closure not supported by this build");
+  if ((long long)Nx * Ny * Nz > (1LL << 31)) return fail(LBM_EINVAL, "too many nodes");
+
+  lbm_s* h = new (std::nothrow) lbm_s();
+  if (!h) return fail(LBM_ENOMEM, "host allocation failed");
+  std::memset(static_cast<Handle*>(h), 0, sizeof(Handle));
+  h->D = D;
+  h->Q = lattice;
+  h->Nx = Nx; h->Ny = Ny; h->Nz = Nz;
+  h->eos = *eos;
+  h->tau = tau; h->Pr = Pr; h->cv = cv;
+  h->precision = eos->precision;
+  h->elem_bytes = eos->precision == LBM_FP64 ? 8 : (eos->precision == LBM_FP32 ? 4 : 2);
+  h->stream = nullptr;
+  Params& p = h->p;
+  p.D = D; p.Q = lattice; p.Nx = Nx; p.Ny = Ny; p.Nz = Nz;
+  p.periodic_x = 1;
+  p.bc_lo = p.bc_hi = LBM_BC_PERIODIC;
+  p.a = eos->a; p.b = eos->b; p.R = eos->R; p.cv = cv;
+  p.kappa = eos->kappa; p.eta_over_mu = eos->eta_over_mu;
+  Model<double> m = host_model(*h);
+  const double P_ref = vdw_pressure(m, eos->rho_ref, eos->T_ref);
+  if (!(P_ref > 0)) {
+    delete h;
+    return fail(LBM_EINVAL, "P(rho_ref, T_ref) must be > 0");
+  }
+  p.mu = tau * P_ref;                                      // tau = mu / P at the reference state
+  const double RT = eos->R * eos->T_ref, x = 1.0 - eos->b * eos->rho_ref;
+  const double cp = cv + eos->R * eos->R * eos->T_ref / (RT - 2.0 * eos->a * eos->rho_ref * x * x);  // Eq. cpvdW
+  p.k_over_mu = cp / Pr;                                   // Pr = mu c_p / k
+  m = host_model(*h);
+  if (h->precision == LBM_FP16DEV) {
+    double feq[27], geq[27], u0[3] = {0, 0, 0};
+    if (D == 2) equilibria<2, double>(m, eos->rho_ref, u0, eos->T_ref, feq, geq);
+    else equilibria<3, double>(m, eos->rho_ref, u0, eos->T_ref, feq, geq);
+    for (int i = 0; i < h->Q; ++i) {
+      p.ref[i] = float(feq[i]);
+      p.ref[h->Q + i] = float(geq[i]);
+    }
+  }
+  int rc;
+  if (cudaMalloc(&h->partials, kMaxPartials * 5 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->totals_dev, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->err_dev, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&h->err_host, sizeof(unsigned)) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "allocation");
+    lbm_destroy(h);
+    return rc;
+  }
+  cudaMemset(h->err_dev, 0, sizeof(unsigned));
+  rc = layout(*h);
+  if (rc != LBM_OK) {
+    std::string msg = g_err;
+    lbm_destroy(h);
+    return fail(rc, msg);
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_set_boundary(lbm_t h, int face, int type, const double* state) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (face != LBM_FACE_XLO && face != LBM_FACE_XHI) return fail(LBM_EINVAL, "face must be XLO or XHI");
+  if (type != LBM_BC_PERIODIC && type != LBM_BC_OUTFLOW && type != LBM_BC_INFLOW)
+    return fail(LBM_EINVAL, "bad boundary type");
+  Params& p = h->p;
+  const int was_periodic = p.periodic_x;
+  if (type == LBM_BC_PERIODIC) {
+    p.bc_lo = p.bc_hi = LBM_BC_PERIODIC;
+    p.periodic_x = 1;
+  } else {
+    if (type == LBM_BC_INFLOW) {
+      if (!state) return fail(LBM_EINVAL, "inflow needs a state");
+      if (!(state[0] > 0) || !(state[h->D + 1] > 0)) return fail(LBM_EINVAL, "inflow rho and T must be > 0");
+      double* st = face == 0 ? p.st_lo : p.st_hi;
+      st[0] = state[0];
+      st[1] = st[2] = st[3] = 0.0;
+      for (int a = 0; a < h->D; ++a) st[1 + a] = state[1 + a];
+      st[4] = state[h->D + 1];
+      set_face_eq(*h, face);
+    }
+    if (was_periodic) {  // the other face becomes outflow until set
+      p.bc_lo = p.bc_hi = LBM_BC_OUTFLOW;
+    }
+    (face == 0 ? p.bc_lo : p.bc_hi) = type;
+    p.periodic_x = 0;
+  }
+  if (was_periodic != p.periodic_x) return layout(*h);
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_t h, void* stream) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+static int init_common(lbm_t h, const double* d_rho, const double* d_u, const double* d_T) {
+  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream));
+  h->cur = 0;
+  ops_for(*h)->init(*h, d_rho, d_u, d_T);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  h->initialized = 1;
+  h->unstable = 0;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_t h, const double* rho, const double* u, const double* T) {
+  if (!h || !rho || !u || !T) return fail(LBM_EINVAL, "NULL argument");
+  const size_t N = size_t(h->Nx) * h->Ny * h->Nz;
+  double* d = h->io_dev;
+  CK(cudaMemcpyAsync(d, rho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(d + N, u, h->D * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(d + (h->D + 1) * N, T, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  return init_common(h, d, d + N, d + (h->D + 1) * N);
+}
+
+int lbm_init_device(lbm_t h, const double* d_rho, const double* d_u, const double* d_T) {
+  if (!h || !d_rho || !d_u || !d_T) return fail(LBM_EINVAL, "NULL argument");
+  return init_common(h, d_rho, d_u, d_T);
+}
+
+int lbm_step_async(lbm_t h, int n) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!h->initialized) return fail(LBM_ESTATE, "lbm_init has not been called");
+  if (h->unstable) return fail(LBM_ESTATE, "state is unstable; call lbm_init");
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  const Ops* o = ops_for(*h);
+  for (int k = 0; k < n; ++k) {
+    o->step(*h, h->pop[h->cur], h->pop[h->cur ^ 1]);
+    h->cur ^= 1;
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_t h) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  return read_err(*h);
+}
+
+int lbm_step(lbm_t h, int n) {
+  int rc = lbm_step_async(h, n);
+  if (rc != LBM_OK) return rc;
+  return read_err(*h);
+}
+
+int lbm_moments_device(lbm_t h, double* d_rho, double* d_u, double* d_T, double* totals) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!h->initialized) return fail(LBM_ESTATE, "lbm_init has not been called");
+  ops_for(*h)->macro(*h, h->pop[h->cur], d_rho, d_u, d_T, totals ? h->totals_dev : nullptr);
+  CK(cudaGetLastError());
+  if (totals)
+    CK(cudaMemcpyAsync(totals, h->totals_dev, (h->D + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_t h, double* rho, double* u, double* T, double* totals) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!h->initialized) return fail(LBM_ESTATE, "lbm_init has not been called");
+  const size_t N = size_t(h->Nx) * h->Ny * h->Nz;
+  double* d = h->io_dev;
+  int rc = lbm_moments_device(h, rho ? d : nullptr, u ? d + N : nullptr, T ? d + (h->D + 1) * N : nullptr, totals);
+  if (rc != LBM_OK) return rc;
+  if (rho) CK(cudaMemcpyAsync(rho, d, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (u) CK(cudaMemcpyAsync(u, d + N, h->D * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (T) CK(cudaMemcpyAsync(T, d + (h->D + 1) * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_get_flags(lbm_t h, unsigned* flags) {
+  if (!h || !flags) return fail(LBM_EINVAL, "NULL argument");
+  CK(cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *flags = *h->err_host;
+  return LBM_OK;
+}
+
+size_t lbm_population_bytes(lbm_t h) {
+  if (!h) return 0;
+  return size_t(2 * h->Q) * size_t(h->p.plane) * h->elem_bytes;
+}
+
+int lbm_get_populations(lbm_t h, void* host, size_t bytes) {
+  if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+  if (bytes != lbm_population_bytes(h)) return fail(LBM_EINVAL, "size mismatch");
+  if (!h->initialized) return fail(LBM_ESTATE, "lbm_init has not been called");
+  CK(cudaMemcpyAsync(host, h->pop[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_t h, const void* host, size_t bytes) {
+  if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
+  if (bytes != lbm_population_bytes(h)) return fail(LBM_EINVAL, "size mismatch");
+  CK(cudaMemcpyAsync(h->pop[h->cur], host, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->initialized = 1;
+  h->unstable = 0;
+  return LBM_OK;
+}
+
+long long lbm_launch_count(lbm_t h) { return h ? h->launches : 0; }
+
+int lbm_destroy(lbm_t h) {
+  if (!h) return LBM_OK;
+  free_state(*h);
+  if (h->partials) cudaFree(h->partials);
+  if (h->totals_dev) cudaFree(h->totals_dev);
+  if (h->err_dev) cudaFree(h->err_dev);
+  if (h->err_host) cudaFreeHost(h->err_host);
+  delete h;
+  return LBM_OK;
+}
+
+}  // extern "C"

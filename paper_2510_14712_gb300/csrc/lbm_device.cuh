@@ -1,0 +1,208 @@
+// lbm_device.cuh - per-node arithmetic of the non-ideal compressible LBM
+// (Hosseini, Feinberg & Karlin, Sec. 3.2), shared by every kernel of the
+// library.  Templated on the dimension D (2: D2Q9, 3: D3Q27) and on the
+// arithmetic type `real` (double for the FP64 build, float otherwise).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Velocity i <-> (c_x, c_y[, c_z]) in {-1,0,1}^D, lexicographic with the last
+// component fastest (Eq. D3Q27c): i = 9 (cx+1) + 3 (cy+1) + (cz+1) in 3-D and
+// i = 3 (cx+1) + (cy+1) in 2-D.
+template <int D> struct Lattice;
+template <> struct Lattice<2> {
+  static constexpr int Q = 9;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a == 0 ? i / 3 - 1 : i % 3 - 1;
+  }
+};
+template <> struct Lattice<3> {
+  static constexpr int Q = 27;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a == 0 ? i / 9 - 1 : (a == 1 ? (i / 3) % 3 - 1 : i % 3 - 1);
+  }
+};
+
+// Model constants in the arithmetic type.
+template <typename real> struct Model {
+  real a, b, R, cv;          // van der Waals (Eq. Pvdw), c_v
+  real kappa;                // Korteweg capillarity (Eq. FK)
+  real eta_over_mu;          // bulk / shear viscosity (Eq. corr_bulk)
+  real mu;                   // shear viscosity (constant, Sec. 2)
+  real k_over_mu;            // thermal conductivity / mu (Eq. qc)
+};
+
+template <typename real> __host__ __device__ inline real vdw_pressure(const Model<real>& m, real rho, real T) {
+  return rho * m.R * T / (real(1) - m.b * rho) - m.a * rho * rho;          // Eq. Pvdw
+}
+template <typename real> __host__ __device__ inline real vdw_energy(const Model<real>& m, real rho, real T) {
+  return m.cv * T - m.a * rho;                                             // Eq. de_vdW, integrated
+}
+template <typename real> __host__ __device__ inline real vdw_cs2(const Model<real>& m, real rho, real T) {
+  const real s = real(1) / (real(1) - m.b * rho);
+  return m.R * T * (real(1) + m.R / m.cv) * s * s - real(2) * m.a * rho;   // Eq. vdW_speed_of_sound
+}
+
+// Eq. phi: Psi(c; xi, zeta) = 1 - zeta (c = 0), (zeta + c xi)/2 (c = +-1).
+// The three values for c = -1, 0, +1 of one axis.
+template <typename real> struct Axis3 {
+  real v[3];
+  __host__ __device__ real operator[](int c) const { return v[c + 1]; }
+};
+template <typename real> __host__ __device__ inline Axis3<real> psi3(real xi, real zeta) {
+  Axis3<real> t;
+  t.v[0] = real(0.5) * (zeta - xi);
+  t.v[1] = real(1) - zeta;
+  t.v[2] = real(0.5) * (zeta + xi);
+  return t;
+}
+// Psi(O, O^2) with O = theta d/du + u (Eq. Oa) applied to u^2/2, the part of
+// the generating function E = e + u^2/2 (Eq. Egen) that depends on u_a:
+//   O(u^2/2)   = theta u + u^3/2                   =: A
+//   O^2(u^2/2) = theta^2 + 5/2 theta u^2 + u^4/2   =: B
+//   factor     = u^2/2 - B (c = 0),  (B + c A)/2 (c = +-1).
+template <typename real> __host__ __device__ inline Axis3<real> chi3(real u, real theta) {
+  const real u2 = u * u;
+  const real A = u * (theta + real(0.5) * u2);
+  const real B = theta * theta + u2 * (real(2.5) * theta + real(0.5) * u2);
+  Axis3<real> t;
+  t.v[0] = real(0.5) * (B - A);
+  t.v[1] = real(0.5) * u2 - B;
+  t.v[2] = real(0.5) * (B + A);
+  return t;
+}
+
+// Equilibria at one state for all i (Fig. FlowChart, "Initialize"):
+// f^eq = rho prod_a Psi(c_ia; u_a, theta + u_a^2)                          (Eq. LBMeq)
+// g^eq = rho [ e prod_a psi_a + sum_b chi_b prod_{a != b} psi_a ]         (Eq. LBMeqG)
+template <int D, typename real>
+__host__ __device__ inline void equilibria(const Model<real>& m, real rho, const real* u, real T, real* feq, real* geq) {
+  using L = Lattice<D>;
+  const real P = vdw_pressure(m, rho, T);
+  const real theta = P / rho;
+  const real e = vdw_energy(m, rho, T);
+  Axis3<real> ps[D], ch[D];
+  for (int a = 0; a < D; ++a) {
+    ps[a] = psi3(u[a], theta + u[a] * u[a]);
+    ch[a] = chi3(u[a], theta);
+  }
+  for (int i = 0; i < L::Q; ++i) {
+    real prod = real(1);
+    for (int a = 0; a < D; ++a) prod *= ps[a][L::c(i, a)];
+    real acc = e * prod;
+    for (int b = 0; b < D; ++b) {
+      real t = ch[b][L::c(i, b)];
+      for (int a = 0; a < D; ++a)
+        if (a != b) t *= ps[a][L::c(i, a)];
+      acc += t;
+    }
+    feq[i] = rho * prod;
+    geq[i] = rho * acc;
+  }
+}
+
+// Fields of one node needed by its neighbours' stencils.
+template <int D, typename real> struct NodeFields {
+  real u[D], T, h, Lam[D];
+};
+
+// Inputs of the collision at one node besides the populations.
+template <int D, typename real> struct NodeState {
+  real rho, u[D], F[D], T;
+  real div_u;            // central divergence of u
+  real gradT[D], gradh[D];
+  real dLam[D];          // upwind derivative of Lambda_a along a (Sec. 3.2)
+};
+
+enum : unsigned { FLAG_NONFINITE = 1u, FLAG_NEGATIVE = 2u, FLAG_THETA = 4u, FLAG_PRESSURE = 8u };
+
+// The collision of Eqs. fLBGK / gLBGK at one node.  f, g: the 2Q pulled
+// (post-streaming) populations in, post-collision populations out.
+// Returns the status bits of this node.
+template <int D, typename real>
+__device__ __forceinline__ unsigned collide_node(const Model<real>& m, const NodeState<D, real>& s, real* f, real* g) {
+  using L = Lattice<D>;
+  const real rho = s.rho, T = s.T;
+  const real inv_rho = real(1) / rho;
+  const real P = vdw_pressure(m, rho, T);
+  const real theta = P * inv_rho;                                          // Eq. theta
+  const real e = vdw_energy(m, rho, T);
+  const real cs2 = vdw_cs2(m, rho, T);
+  const real alpha = real(D + 2) / real(D) - rho * cs2 / P - m.eta_over_mu;   // Eq. corr_bulk
+  const real tau = m.mu / P;                                               // tau = mu / P
+  const real beta = real(1) / (real(2) * tau + real(1));                   // Eq. beta_main
+  const real twobeta = real(2) * beta, omb = real(1) - beta;
+
+  // shifted state (Eqs. sh_vel_1, sh_temp_1, sh_T_1, qc_1; delta t = 1)
+  real us[D], FF = real(0);
+  for (int a = 0; a < D; ++a) {
+    us[a] = s.u[a] + s.F[a] * inv_rho;
+    FF += s.F[a] * s.F[a];
+  }
+  const real theta_s = theta + alpha * theta * s.div_u;
+  const real T_s = T - FF * real(0.5) * inv_rho * inv_rho / m.cv;
+  const real e_s = vdw_energy(m, rho, T_s);
+  real qc[D];
+  for (int a = 0; a < D; ++a) qc[a] = P * (s.gradh[a] - m.k_over_mu * s.gradT[a]);
+
+  // per-axis product-form tables
+  Axis3<real> pe[D], pf[D], pg[D], ce[D], cg[D];
+  for (int a = 0; a < D; ++a) {
+    const real Phi = -s.dLam[a] * inv_rho;                                 // Eq. correction
+    pe[a] = psi3(s.u[a], theta + s.u[a] * s.u[a]);                         // Eqs. def_xi_eq, def_zeta_eq
+    pf[a] = psi3(us[a], theta_s + us[a] * us[a] + Phi);                    // Eqs. xistar, zetastar
+    pg[a] = psi3(us[a], theta_s + us[a] * us[a]);                          // g* : no Phi
+    ce[a] = chi3(s.u[a], theta);
+    cg[a] = chi3(us[a], theta_s);
+  }
+
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    int c[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) c[a] = L::c(i, a);
+    real pe_all = rho, pf_all = rho, pg_all = real(1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      pe_all *= pe[a][c[a]];
+      pf_all *= pf[a][c[a]];
+      pg_all *= pg[a][c[a]];
+    }
+    // g^eq = rho [e prod psi + sum_b chi_b prod_{a!=b} psi]; g* the same at the star state
+    real ge = e * pe_all, gs = e_s * rho * pg_all;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      real te = ce[b][c[b]] * rho, tg = cg[b][c[b]] * rho;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (a != b) {
+          te *= pe[a][c[a]];
+          tg *= pg[a][c[a]];
+        }
+      ge += te;
+      gs += tg;
+    }
+    int nz = 0;
+    real cq = real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      nz += c[a] != 0;
+      cq += real(c[a]) * qc[a];
+    }
+    if (nz == 1) gs += real(0.5) * cq;                                     // Eq. LBMgstar, |c_i|^2 = 1
+    const real fe = pe_all;
+    f[i] = f[i] + twobeta * (fe - f[i]) + omb * (pf_all - fe);             // Eq. fLBGK
+    g[i] = g[i] + twobeta * (ge - g[i]) + omb * (gs - ge);                 // Eq. gLBGK
+  }
+  unsigned flags = 0;
+  if (!(isfinite(rho) && isfinite(T))) flags |= FLAG_NONFINITE;
+  if (!(rho > real(0)) || !(T > real(0))) flags |= FLAG_NEGATIVE;
+  if (theta >= real(1.0 / 3.0)) flags |= FLAG_THETA;
+  if (!(P > real(0))) flags |= FLAG_PRESSURE;
+  return flags;
+}
+
+}  // namespace lbm

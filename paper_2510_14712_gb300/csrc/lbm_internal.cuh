@@ -1,0 +1,84 @@
+// lbm_internal.cuh - handle, kernel parameters and the dispatch table that
+// the C interface (lbm_capi.cu) uses to reach the per-lattice /
+// per-precision kernel instantiations (k_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kGhost = 4;         // ghost layers per non-periodic x face
+constexpr int kMaxPartials = 1024;
+
+// Everything a kernel needs, passed by value.
+struct Params {
+  // geometry: padded x index xp = x + G; node offset = (z*Ny + y)*pitch + xp
+  int D, Q, Nx, Ny, Nz, G, pitch;
+  long long plane;            // elements per population plane = Nz*Ny*pitch
+  int periodic_x;
+  int bc_lo, bc_hi;           // LBM_BC_* of the x faces
+  // model (FP64 master copy)
+  double a, b, R, cv, kappa, eta_over_mu, mu, k_over_mu;
+  // inflow states (rho, u[3], T) and their equilibria (post-collision ghosts)
+  double st_lo[5], st_hi[5];
+  double eq_lo[54], eq_hi[54];   // f then g
+  // FP16-deviation reference populations (f then g)
+  float ref[54];
+};
+
+template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
+  Model<real> m;
+  m.a = real(p.a); m.b = real(p.b); m.R = real(p.R); m.cv = real(p.cv);
+  m.kappa = real(p.kappa); m.eta_over_mu = real(p.eta_over_mu);
+  m.mu = real(p.mu); m.k_over_mu = real(p.k_over_mu);
+  return m;
+}
+
+// One solver instance.
+struct Handle {
+  int D, Q, Nx, Ny, Nz;
+  lbm_eos eos;
+  double tau, Pr, cv;
+  Params p;
+  int precision;
+  size_t elem_bytes;          // bytes per stored population value
+  void* pop[2];               // ping-pong population buffers
+  int cur;                    // index of the buffer holding the current state
+  void* scratch;              // moment / primitive fields of the multi-pass path
+  size_t scratch_bytes;
+  double* partials;           // kMaxPartials*(D+2) reduction partials
+  double* totals_dev;         // D+2
+  unsigned* err_dev;          // sticky status word
+  unsigned* err_host;         // pinned
+  double* io_dev;             // staging for host <-> device field copies
+  size_t io_bytes;
+  cudaStream_t stream;
+  int initialized, unstable;
+  long long launches;
+};
+
+// Per (D, precision) kernel set.
+struct Ops {
+  // state[i] at every padded node from FP64 device fields (interior layout)
+  void (*init)(Handle& h, const double* rho, const double* u, const double* T);
+  // one step: pop[cur] -> pop[cur^1] (including the ghost fill)
+  void (*step)(Handle& h, const void* src, void* dst);
+  // macroscopic FP64 fields of pop[cur] into device outputs (any may be NULL);
+  // totals (device, D+2 doubles) when non-NULL
+  void (*macro)(Handle& h, const void* src, double* rho, double* u, double* T, double* totals);
+};
+
+const Ops* ops_d2_fp64();
+const Ops* ops_d2_fp32();
+const Ops* ops_d3_fp64();
+const Ops* ops_d3_fp32();
+const Ops* ops_d2_fp16();
+const Ops* ops_d3_fp16();
+
+}  // namespace lbm

@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C interface) against the FP64 oracle.
+
+Tolerances (relative L2 over the interior, per field rho, u, T): 1e-12 for
+the FP64 build and 1e-5 for the FP32 build after the stated steps.  Inputs
+are the seeded synthetic workloads of ``inputs`` at sizes the oracle
+finishes in seconds, with ragged extents so that no dimension is a
+multiple of a tile; the full-size Taylor-Green workload is checked on
+sampled nodes against the oracle evaluated on a window around each sample.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import inputs
+from parity_util import assert_parity, gpu_run, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2510_14712_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_14712_gb300 import build
+    build.build()
+    P.load()
+
+
+def tgv_case(shape, nu=0.02, seed=0):
+    """Seeded Taylor-Green vortex at a viscosity the small grid resolves."""
+    c = inputs.add_noise(inputs.tgv(shape=shape), seed)
+    sc = inputs.scenario("tgv_d3q27")
+    c.tau = sc["tau"] * nu / sc["nu"]
+    return c
+
+
+def shock_case(Nx=400, Ny=3, Ma=1.2):
+    from oracle import thermo
+    sc = copy.deepcopy(inputs.scenario("shock_drop_d2q9"))
+    e, v = sc["eos"], sc["vapour"]
+    r2, T2, u2, _ = thermo.rankine_hugoniot(v["rho"], v["T"], 0.0, Ma, e["a"], e["b"], e["R"], sc["cv"])
+    sc["post"] = dict(rho=r2, T=T2, u=u2)
+    return inputs.add_noise(inputs.shock_drop(2, (Nx, Ny), shock_x=60, with_drop=False, sc=sc), 3)
+
+
+# ---- config 1: D2Q9 Riemann problem, 1000 x 4, 1000 steps -----------------------
+
+@pytest.fixture(scope="module")
+def riemann_ref():
+    return oracle_run(inputs.riemann(), 1000)
+
+
+def test_riemann_fp64(riemann_ref):
+    got = gpu_run(inputs.riemann(), 1000, "fp64")
+    assert_parity(got, riemann_ref, 1e-12, "riemann fp64")
+    assert np.allclose(got["totals"], riemann_ref["totals"], rtol=1e-12, atol=1e-12)
+
+
+def test_riemann_fp32(riemann_ref):
+    got = gpu_run(inputs.riemann(), 1000, "fp32")
+    assert_parity(got, riemann_ref, 1e-5, "riemann fp32")
+
+
+# ---- D3Q27 Taylor-Green with noise on a ragged box -------------------------------
+
+@pytest.fixture(scope="module")
+def tgv_ref():
+    return oracle_run(tgv_case((37, 21, 13)), 100)
+
+
+def test_tgv_d3q27_fp64(tgv_ref):
+    got = gpu_run(tgv_case((37, 21, 13)), 100, "fp64")
+    assert_parity(got, tgv_ref, 1e-12, "tgv fp64")
+
+
+def test_tgv_d3q27_fp32(tgv_ref):
+    got = gpu_run(tgv_case((37, 21, 13)), 100, "fp32")
+    assert_parity(got, tgv_ref, 1e-5, "tgv fp32")
+
+
+def test_tgv_d3q27_fp64_long():
+    c = tgv_case((19, 13, 11), seed=5)
+    want = oracle_run(c, 1000)
+    got = gpu_run(tgv_case((19, 13, 11), seed=5), 1000, "fp64", chunk=250)
+    assert_parity(got, want, 1e-12, "tgv fp64 1000 steps")
+
+
+def test_tgv_d3q27_fp32_long():
+    want = oracle_run(tgv_case((19, 13, 11), seed=5), 1000)
+    got = gpu_run(tgv_case((19, 13, 11), seed=5), 1000, "fp32")
+    assert_parity(got, want, 1e-5, "tgv fp32 1000 steps")
+
+
+# ---- D2Q9 shock tube with inflow / outflow faces ---------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_shock_tube(precision, tol):
+    want = oracle_run(shock_case(), 300)
+    got = gpu_run(shock_case(), 300, precision)
+    assert_parity(got, want, tol, "shock tube " + precision)
+
+
+# ---- edge cases --------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(5, 1), (1, 6), (3, 2)])
+def test_degenerate_2d_extents(shape):
+    """One-node-wide periodic directions (Ny = 1 or Nx = 1) and tiny boxes."""
+    sc = inputs.scenario("tgv_d3q27")
+    c = inputs.Case(name="tgv_d3q27", D=2, shape=shape, eos=dict(sc["eos"]), tau=0.1, Pr=0.71, cv=sc["cv"])
+    arr = tuple(reversed(shape))
+    n = int(np.prod(shape))
+    c.rho = sc["rho0"] * (1 + 0.01 * inputs.uniform(1, n).reshape(arr))
+    c.T = sc["T0"] * (1 + 0.01 * inputs.uniform(2, n).reshape(arr))
+    c.u = [0.02 * inputs.uniform(3 + a, n).reshape(arr) for a in range(2)]
+    want = oracle_run(c, 50)
+    got = gpu_run(c, 50, "fp64")
+    assert_parity(got, want, 1e-12, "degenerate %s" % (shape,))
+
+
+def test_uniform_state_fixed_point():
+    c = tgv_case((9, 7, 5))
+    c.rho = np.full_like(c.rho, 0.6)
+    c.T = np.full_like(c.T, inputs.scenario("tgv_d3q27")["T0"])
+    c.u = [np.full_like(c.rho, v) for v in (0.05, -0.02, 0.03)]
+    got = gpu_run(c, 25, "fp64")
+    assert np.abs(got["rho"] - 0.6).max() < 1e-14
+    for a, v in enumerate((0.05, -0.02, 0.03)):
+        assert np.abs(got["u"][a] - v).max() < 1e-14
+
+
+def test_conservation_totals_gpu():
+    """Periodic box: mass and momentum are exact invariants (sum F = 0 for the compact stencils)."""
+    c = tgv_case((23, 17, 9))
+    s = P.Solver(c, precision="fp64")
+    try:
+        s.init()
+        t0 = s.fields()["totals"]
+        s.step(40)
+        t1 = s.fields()["totals"]
+    finally:
+        s.close()
+    assert abs(t1[0] - t0[0]) < 1e-12 * t0[0]
+    assert np.abs(t1[1:4] - t0[1:4]).max() < 1e-12 * t0[0]
+
+
+def test_zero_steps_and_state_errors():
+    c = tgv_case((8, 6, 5))
+    s = P.Solver(c, precision="fp32")
+    try:
+        with pytest.raises(P.LbmError) as ei:
+            s.step(1)
+        assert ei.value.code == P.LBM_ESTATE
+        s.init()
+        before = s.fields()
+        s.step(0)
+        after = s.fields()
+        assert np.array_equal(before["rho"], after["rho"])
+        with pytest.raises(P.LbmError) as ei:
+            P.lbm_step(s.h, -1)
+        assert ei.value.code == P.LBM_EINVAL
+    finally:
+        s.close()
+
+
+def test_nonfinite_input_reports_unstable_then_recovers():
+    """A NaN planted in the initial density raises LBM_EUNSTABLE; steps are refused until re-init."""
+    c = tgv_case((8, 6, 5))
+    rho = c.rho.copy()
+    rho[2, 3, 4] = np.nan
+    s = P.Solver(c, precision="fp32")
+    try:
+        s.init(rho=rho)
+        with pytest.raises(P.LbmError) as ei:
+            s.step(2)
+        assert ei.value.code == P.LBM_EUNSTABLE
+        assert P.lbm_get_flags(s.h) & P.LBM_FLAG_NONFINITE
+        with pytest.raises(P.LbmError) as ei:
+            s.step(1)
+        assert ei.value.code == P.LBM_ESTATE
+        s.init()
+        s.step(3)
+        assert P.lbm_get_flags(s.h) & (P.LBM_FLAG_NONFINITE | P.LBM_FLAG_NEGATIVE) == 0
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_bit_identical(precision):
+    c = tgv_case((14, 9, 6))
+    s = P.Solver(c, precision=precision)
+    try:
+        s.init().step(7)
+        ck = P.lbm_get_populations(s.h)
+        s.step(9)
+        a = s.fields()
+        P.lbm_set_populations(s.h, ck)
+        s.step(9)
+        b = s.fields()
+    finally:
+        s.close()
+    for k in ("rho", "u", "T"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_riemann_chunked_equals_single_call():
+    a = gpu_run(inputs.riemann(Nx=200, Ny=4), 60, "fp32")
+    b = gpu_run(inputs.riemann(Nx=200, Ny=4), 60, "fp32", chunk=7)
+    for k in ("rho", "u", "T"):
+        assert np.array_equal(a[k], b[k])
+
+
+# ---- full size: the benchmark workload, sampled nodes --------------------------------
+
+def window_oracle_one_step(case, centers, r=7):
+    """Oracle step on a (2r+1)^3 periodic window around each node; the centre is exact for r >= 6.
+
+    A post-step moment at x needs the post-collision populations within
+    radius 3 of x (rho to radius 2 for F, plus the pull), each of which
+    needs the pre-step state within radius 3: radius 6 in all.
+    """
+    from oracle import lbm as olbm
+    out = []
+    Nx, Ny, Nz = case.shape
+    for (x, y, z) in centers:
+        ix = np.arange(x - r, x + r + 1) % Nx
+        iy = np.arange(y - r, y + r + 1) % Ny
+        iz = np.arange(z - r, z + r + 1) % Nz
+        sel = np.ix_(iz, iy, ix)
+        n = 2 * r + 1
+        m = olbm.Model(3, (n, n, n), case.eos, case.tau, case.Pr, case.cv)
+        s = olbm.Sim(m, case.rho[sel], [ua[sel] for ua in case.u], case.T[sel])
+        s.step(1)
+        F = s.fields()
+        out.append((F["rho"][r, r, r], [F["u"][a][r, r, r] for a in range(3)], F["T"][r, r, r]))
+    return out
+
+
+def test_full_size_tgv_256_sampled_fp32():
+    """The benchmark's workload (D3Q27 256^3 Taylor-Green, FP32), one step, 24 sampled nodes."""
+    case = inputs.tgv(N=256)
+    got = gpu_run(case, 1, "fp32")
+    rng = np.random.default_rng(11)
+    centers = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(24)] + [(0, 0, 0), (255, 255, 255)]
+    ref = window_oracle_one_step(case, centers)
+    for (x, y, z), (r0, u0, t0) in zip(centers, ref):
+        assert abs(got["rho"][z, y, x] / r0 - 1) < 1e-6
+        assert abs(got["T"][z, y, x] / t0 - 1) < 1e-6
+        for a in range(3):
+            assert abs(got["u"][a][z, y, x] - u0[a]) < 1e-6 * (abs(u0[a]) + 1e-2)
+    # properties at full size: mass and momentum of the periodic box are unchanged
+    s = P.Solver(case, precision="fp32")
+    try:
+        s.init()
+        t0 = s.fields()["totals"]
+        s.step(3)
+        t1 = s.fields()["totals"]
+    finally:
+        s.close()
+    assert abs(t1[0] / t0[0] - 1) < 1e-6
+    assert np.abs(t1[1:4] - t0[1:4]).max() < 1e-6 * t0[0]
