@@ -131,6 +131,26 @@ def g_equilibrium(rho, u, theta, e, c):
     return np.array(out)
 
 
+def first_moment(f, c, a):
+    """sum_i c_ia f_i (Eqs. def_u, transform_u), summed over mirror pairs.
+
+    Each direction with c_ia = +1 is paired with its mirror image in axis a
+    (c_ia = -1, other components equal) and the sum runs over the differences
+    f_i - f_mirror.  This is the same sum reassociated; it is exactly zero
+    whenever the populations are mirror-symmetric, so that a state at rest
+    has u = 0 exactly and the upwind stencil of Sec. 3.2 takes its sgn(0)
+    (central) branch, as it does in exact arithmetic.
+    """
+    acc = np.zeros_like(f[0])
+    for i, ci in enumerate(c):
+        if ci[a] == 1:
+            mirror = list(ci)
+            mirror[a] = -1
+            k = int(np.nonzero(np.all(c == np.array(mirror), axis=1))[0][0])
+            acc = acc + (f[i] - f[k])
+    return acc
+
+
 def velocity(j, F, rho):
     """u = (sum c_i f_i + F/2) / rho (Eq. def_u with delta t = 1)."""
     return [(j[a] + 0.5 * F[a]) / rho for a in range(len(j))]
@@ -270,7 +290,7 @@ class Sim:
         g = self.g if g is None else g
         D = m.D
         rho = f.sum(axis=0)                                           # Eq. def_h
-        j = [np.tensordot(m.c[:, a].astype(np.float64), f, axes=1) for a in range(D)]
+        j = [first_moment(f, m.c, a) for a in range(D)]
         S = g.sum(axis=0)
         lap = sum(m.nb(rho, a, 1) - 2.0 * rho + m.nb(rho, a, -1) for a in range(D))
         F = [m.kappa * rho * 0.5 * (m.nb(lap, a, 1) - m.nb(lap, a, -1)) for a in range(D)]

@@ -26,6 +26,24 @@ template <> struct Lattice<3> {
   }
 };
 
+// sum_i c_ia f_i (Eq. def_u) as a sum over mirror pairs: each direction with
+// c_ia = +1 minus its mirror image in axis a.  Exactly zero for
+// mirror-symmetric populations, so that a fluid at rest has u = 0 exactly and
+// the upwind stencil takes its sgn(0) branch as in exact arithmetic.
+template <int D, typename real> __device__ __forceinline__ void first_moment(const real* f, real* j) {
+  using L = Lattice<D>;
+  constexpr int stride0 = D == 3 ? 9 : 3, stride1 = D == 3 ? 3 : 1, stride2 = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int st = a == 0 ? stride0 : (a == 1 ? stride1 : stride2);
+    real acc = real(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      if (L::c(i, a) == 1) acc += f[i] - f[i - 2 * st];
+    j[a] = acc;
+  }
+}
+
 // Model constants in the arithmetic type.
 template <typename real> struct Model {
   real a, b, R, cv;          // van der Waals (Eq. Pvdw), c_v

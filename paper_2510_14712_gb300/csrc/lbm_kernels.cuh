@@ -163,14 +163,12 @@ __global__ void k_moments(Params p, const typename Store<S>::T* A, real* M) {
   real fg[2 * L::Q];
   pull<D, S, real>(p, A, xp, y, z, fg);
   real rho = 0, j[D], Se = 0;
-  for (int a = 0; a < D; ++a) j[a] = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     rho += fg[i];
     Se += fg[L::Q + i];
-#pragma unroll
-    for (int a = 0; a < D; ++a) j[a] += real(L::c(i, a)) * fg[i];
   }
+  first_moment<D, real>(fg, j);
   const long long o = node_off(p, xp, y, z);
   M[o] = rho;
   for (int a = 0; a < D; ++a) M[(1 + a) * p.plane + o] = j[a];
