@@ -211,7 +211,8 @@ def run_ours(args):
         prec = args.precision
     N = case.nodes
     stream = torch.cuda.current_stream(dev)
-    solver = P.Solver(case, precision=prec, stream=stream.cuda_stream)
+    sk = P.LBM_STEP_MULTIPASS if args.step_kernel == "multipass" else P.LBM_STEP_FUSED
+    solver = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
     rho = torch.from_numpy(np.ascontiguousarray(case.rho, dtype=np.float64)).to(dev)
     u = torch.from_numpy(np.ascontiguousarray(np.stack(case.u), dtype=np.float64)).to(dev)
     T = torch.from_numpy(np.ascontiguousarray(case.T, dtype=np.float64)).to(dev)
@@ -267,7 +268,7 @@ def run_ours(args):
         o_rho, o_u, o_T = torch.empty_like(h_rho).pin_memory(), torch.empty_like(h_u).pin_memory(), \
             torch.empty_like(h_T).pin_memory()
         tot = np.empty(case.D + 2)
-        s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream)
+        s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
         lib = P.load()
         import ctypes
         vp = lambda t: ctypes.c_void_p(t.data_ptr())
@@ -300,7 +301,7 @@ def run_ours(args):
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "step (all launches of one time step)",
+                         "kernel": "step (%s: all launches of one time step)" % args.step_kernel,
                          "algorithmic_bytes_per_step": alg_bytes, "peak_source": peak_kind},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "status_flags": flags,
         }
@@ -320,6 +321,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv256", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp16dev"])
+    ap.add_argument("--step-kernel", default="fused", choices=["fused", "multipass"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -178,6 +178,16 @@ size_t lbm_population_bytes(lbm_t h);
 int lbm_get_populations(lbm_t h, void* host, size_t bytes);
 int lbm_set_populations(lbm_t h, const void* host, size_t bytes);
 
+/* step implementations (lbm_set_step_kernel) */
+enum { LBM_STEP_FUSED = 0, LBM_STEP_MULTIPASS = 1 };
+
+/* Select how lbm_step runs one time step: LBM_STEP_FUSED (default) is one
+ * single-pass kernel per step (plus the ghost fill when x is not periodic);
+ * LBM_STEP_MULTIPASS runs moments, primitive fields and collision as three
+ * kernels through FP-typed scratch fields.  Both compute the same update.
+ * Errors: LBM_EINVAL (NULL handle or unknown kind). */
+int lbm_set_step_kernel(lbm_t h, int kind);
+
 /* Kernel launches enqueued by this handle since creation (for accounting). */
 long long lbm_launch_count(lbm_t h);
 

@@ -24,13 +24,14 @@ LBM_CLOSURE_EXACT, LBM_CLOSURE_MLP = 0, 1
 LBM_BC_PERIODIC, LBM_BC_OUTFLOW, LBM_BC_INFLOW = 0, 1, 2
 LBM_FACE_XLO, LBM_FACE_XHI = 0, 1
 LBM_FLAG_NONFINITE, LBM_FLAG_NEGATIVE, LBM_FLAG_THETA, LBM_FLAG_PRESSURE = 1, 2, 4, 8
+LBM_STEP_FUSED, LBM_STEP_MULTIPASS = 0, 1
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
 
 # every symbol include/lbm.h declares (checked by tests/test_abi.py)
 EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
-           "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version")
+           "lbm_set_step_kernel", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version")
 
 
 class LbmError(RuntimeError):
@@ -75,6 +76,7 @@ def load():
         "lbm_population_bytes": (S, [P]),
         "lbm_get_populations": (I, [P, P, S]),
         "lbm_set_populations": (I, [P, P, S]),
+        "lbm_set_step_kernel": (I, [P, I]),
         "lbm_launch_count": (ctypes.c_longlong, [P]),
         "lbm_destroy": (I, [P]),
         "lbm_last_error": (ctypes.c_char_p, []),
@@ -196,6 +198,10 @@ def lbm_set_populations(h, buf):
     _check(load().lbm_set_populations(h, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
 
 
+def lbm_set_step_kernel(h, kind):
+    _check(load().lbm_set_step_kernel(h, kind))
+
+
 def lbm_launch_count(h):
     return load().lbm_launch_count(h)
 
@@ -214,7 +220,7 @@ def lbm_version():
 class Solver:
     """One handle set up from an ``inputs.Case``-like description."""
 
-    def __init__(self, case, precision="fp64", stream=None):
+    def __init__(self, case, precision="fp64", stream=None, step_kernel=LBM_STEP_FUSED):
         self.case = case
         self.D = case.D
         Nx, Ny = case.shape[0], case.shape[1]
@@ -223,6 +229,7 @@ class Solver:
         self.h = lbm_create(case.lattice, Nx, Ny, Nz, case.eos, case.tau, case.Pr, case.cv, precision)
         if stream:
             lbm_set_stream(self.h, stream)
+        lbm_set_step_kernel(self.h, step_kernel)
         for face, spec in ((LBM_FACE_XLO, case.x_low), (LBM_FACE_XHI, case.x_high)):
             if spec == "periodic":
                 continue

@@ -272,8 +272,9 @@ int lbm_step_async(lbm_t h, int n) {
   if (h->unstable) return fail(LBM_ESTATE, "state is unstable; call lbm_init");
   if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
   const Ops* o = ops_for(*h);
+  auto fn = h->step_kernel == LBM_STEP_MULTIPASS ? o->step_multipass : o->step;
   for (int k = 0; k < n; ++k) {
-    o->step(*h, h->pop[h->cur], h->pop[h->cur ^ 1]);
+    fn(*h, h->pop[h->cur], h->pop[h->cur ^ 1]);
     h->cur ^= 1;
   }
   CK(cudaGetLastError());
@@ -346,6 +347,13 @@ int lbm_set_populations(lbm_t h, const void* host, size_t bytes) {
   CK(cudaStreamSynchronize(h->stream));
   h->initialized = 1;
   h->unstable = 0;
+  return LBM_OK;
+}
+
+int lbm_set_step_kernel(lbm_t h, int kind) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (kind != LBM_STEP_FUSED && kind != LBM_STEP_MULTIPASS) return fail(LBM_EINVAL, "unknown step kernel");
+  h->step_kernel = kind;
   return LBM_OK;
 }
 

@@ -137,90 +137,120 @@ template <int D, typename real> struct NodeState {
 
 enum : unsigned { FLAG_NONFINITE = 1u, FLAG_NEGATIVE = 2u, FLAG_THETA = 4u, FLAG_PRESSURE = 8u };
 
+// The attractors and relaxation factors of one node (Eqs. LBMeq, LBMstar,
+// LBMeqG, LBMgstar, beta_main), as per-axis tables, so that each population
+// can be relaxed on its own (Eqs. fLBGK, gLBGK): the kernels stream the f and
+// the g populations through one direction at a time.
+template <int D, typename real> struct Attractors {
+  real rho, e, e_s, twobeta, omb;
+  real qc[D];
+  Axis3<real> pe[D], pf[D], pg[D], ce[D], cg[D];
+  unsigned flags;
+
+  __device__ __forceinline__ void setup(const Model<real>& m, const NodeState<D, real>& s) {
+    rho = s.rho;
+    const real T = s.T;
+    const real inv_rho = real(1) / rho;
+    const real P = vdw_pressure(m, rho, T);
+    const real theta = P * inv_rho;                                        // Eq. theta
+    e = vdw_energy(m, rho, T);
+    const real cs2 = vdw_cs2(m, rho, T);
+    const real alpha = real(D + 2) / real(D) - rho * cs2 / P - m.eta_over_mu;   // Eq. corr_bulk
+    const real tau = m.mu / P;                                             // tau = mu / P
+    const real beta = real(1) / (real(2) * tau + real(1));                 // Eq. beta_main
+    twobeta = real(2) * beta;
+    omb = real(1) - beta;
+    // shifted state (Eqs. sh_vel_1, sh_temp_1, sh_T_1, qc_1; delta t = 1)
+    real us[D], FF = real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      us[a] = s.u[a] + s.F[a] * inv_rho;
+      FF += s.F[a] * s.F[a];
+    }
+    const real theta_s = theta + alpha * theta * s.div_u;
+    const real T_s = T - FF * real(0.5) * inv_rho * inv_rho / m.cv;
+    e_s = vdw_energy(m, rho, T_s);
+#pragma unroll
+    for (int a = 0; a < D; ++a) qc[a] = P * (s.gradh[a] - m.k_over_mu * s.gradT[a]);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const real Phi = -s.dLam[a] * inv_rho;                               // Eq. correction
+      pe[a] = psi3(s.u[a], theta + s.u[a] * s.u[a]);                       // Eqs. def_xi_eq, def_zeta_eq
+      pf[a] = psi3(us[a], theta_s + us[a] * us[a] + Phi);                  // Eqs. xistar, zetastar
+      pg[a] = psi3(us[a], theta_s + us[a] * us[a]);                        // g*: no Phi
+      ce[a] = chi3(s.u[a], theta);
+      cg[a] = chi3(us[a], theta_s);
+    }
+    flags = 0;
+    if (!(isfinite(rho) && isfinite(T))) flags |= FLAG_NONFINITE;
+    if (!(rho > real(0)) || !(T > real(0))) flags |= FLAG_NEGATIVE;
+    if (theta >= real(1.0 / 3.0)) flags |= FLAG_THETA;
+    if (!(P > real(0))) flags |= FLAG_PRESSURE;
+  }
+
+  // f_i + 2 beta (f_i^eq - f_i) + (1 - beta)(f_i^* - f_i^eq)      (Eq. fLBGK)
+  // (I is a compile-time constant after loop unrolling)
+  __device__ __forceinline__ real relax_f(int I, real f) const {
+    using L = Lattice<D>;
+    real fe = rho, fs = rho;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      fe *= pe[a][L::c(I, a)];
+      fs *= pf[a][L::c(I, a)];
+    }
+    return f + twobeta * (fe - f) + omb * (fs - fe);
+  }
+
+  // g_i + 2 beta (g_i^eq - g_i) + (1 - beta)(g_i^* - g_i^eq)      (Eq. gLBGK)
+  __device__ __forceinline__ real relax_g(int I, real g) const {
+    using L = Lattice<D>;
+    real ge = e, gs = e_s, pe_all = real(1), pg_all = real(1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      pe_all *= pe[a][L::c(I, a)];
+      pg_all *= pg[a][L::c(I, a)];
+    }
+    ge *= pe_all;
+    gs *= pg_all;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      real te = ce[b][L::c(I, b)], tg = cg[b][L::c(I, b)];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (a != b) {
+          te *= pe[a][L::c(I, a)];
+          tg *= pg[a][L::c(I, a)];
+        }
+      ge += te;
+      gs += tg;
+    }
+    ge *= rho;
+    gs *= rho;
+    int nz = 0;
+    real cq = real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      nz += L::c(I, a) != 0;
+      cq += real(L::c(I, a)) * qc[a];
+    }
+    if (nz == 1) gs += real(0.5) * cq;                                     // Eq. LBMgstar, |c_i|^2 = 1
+    return g + twobeta * (ge - g) + omb * (gs - ge);
+  }
+};
+
 // The collision of Eqs. fLBGK / gLBGK at one node.  f, g: the 2Q pulled
 // (post-streaming) populations in, post-collision populations out.
 // Returns the status bits of this node.
 template <int D, typename real>
 __device__ __forceinline__ unsigned collide_node(const Model<real>& m, const NodeState<D, real>& s, real* f, real* g) {
-  using L = Lattice<D>;
-  const real rho = s.rho, T = s.T;
-  const real inv_rho = real(1) / rho;
-  const real P = vdw_pressure(m, rho, T);
-  const real theta = P * inv_rho;                                          // Eq. theta
-  const real e = vdw_energy(m, rho, T);
-  const real cs2 = vdw_cs2(m, rho, T);
-  const real alpha = real(D + 2) / real(D) - rho * cs2 / P - m.eta_over_mu;   // Eq. corr_bulk
-  const real tau = m.mu / P;                                               // tau = mu / P
-  const real beta = real(1) / (real(2) * tau + real(1));                   // Eq. beta_main
-  const real twobeta = real(2) * beta, omb = real(1) - beta;
-
-  // shifted state (Eqs. sh_vel_1, sh_temp_1, sh_T_1, qc_1; delta t = 1)
-  real us[D], FF = real(0);
-  for (int a = 0; a < D; ++a) {
-    us[a] = s.u[a] + s.F[a] * inv_rho;
-    FF += s.F[a] * s.F[a];
+  Attractors<D, real> at;
+  at.setup(m, s);
+#pragma unroll
+  for (int i = 0; i < Lattice<D>::Q; ++i) {
+    f[i] = at.relax_f(i, f[i]);
+    g[i] = at.relax_g(i, g[i]);
   }
-  const real theta_s = theta + alpha * theta * s.div_u;
-  const real T_s = T - FF * real(0.5) * inv_rho * inv_rho / m.cv;
-  const real e_s = vdw_energy(m, rho, T_s);
-  real qc[D];
-  for (int a = 0; a < D; ++a) qc[a] = P * (s.gradh[a] - m.k_over_mu * s.gradT[a]);
-
-  // per-axis product-form tables
-  Axis3<real> pe[D], pf[D], pg[D], ce[D], cg[D];
-  for (int a = 0; a < D; ++a) {
-    const real Phi = -s.dLam[a] * inv_rho;                                 // Eq. correction
-    pe[a] = psi3(s.u[a], theta + s.u[a] * s.u[a]);                         // Eqs. def_xi_eq, def_zeta_eq
-    pf[a] = psi3(us[a], theta_s + us[a] * us[a] + Phi);                    // Eqs. xistar, zetastar
-    pg[a] = psi3(us[a], theta_s + us[a] * us[a]);                          // g* : no Phi
-    ce[a] = chi3(s.u[a], theta);
-    cg[a] = chi3(us[a], theta_s);
-  }
-
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    int c[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) c[a] = L::c(i, a);
-    real pe_all = rho, pf_all = rho, pg_all = real(1);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      pe_all *= pe[a][c[a]];
-      pf_all *= pf[a][c[a]];
-      pg_all *= pg[a][c[a]];
-    }
-    // g^eq = rho [e prod psi + sum_b chi_b prod_{a!=b} psi]; g* the same at the star state
-    real ge = e * pe_all, gs = e_s * rho * pg_all;
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      real te = ce[b][c[b]] * rho, tg = cg[b][c[b]] * rho;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        if (a != b) {
-          te *= pe[a][c[a]];
-          tg *= pg[a][c[a]];
-        }
-      ge += te;
-      gs += tg;
-    }
-    int nz = 0;
-    real cq = real(0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      nz += c[a] != 0;
-      cq += real(c[a]) * qc[a];
-    }
-    if (nz == 1) gs += real(0.5) * cq;                                     // Eq. LBMgstar, |c_i|^2 = 1
-    const real fe = pe_all;
-    f[i] = f[i] + twobeta * (fe - f[i]) + omb * (pf_all - fe);             // Eq. fLBGK
-    g[i] = g[i] + twobeta * (ge - g[i]) + omb * (gs - ge);                 // Eq. gLBGK
-  }
-  unsigned flags = 0;
-  if (!(isfinite(rho) && isfinite(T))) flags |= FLAG_NONFINITE;
-  if (!(rho > real(0)) || !(T > real(0))) flags |= FLAG_NEGATIVE;
-  if (theta >= real(1.0 / 3.0)) flags |= FLAG_THETA;
-  if (!(P > real(0))) flags |= FLAG_PRESSURE;
-  return flags;
+  return at.flags;
 }
 
 }  // namespace lbm

@@ -60,6 +60,7 @@ struct Handle {
   size_t io_bytes;
   cudaStream_t stream;
   int initialized, unstable;
+  int step_kernel;            // LBM_STEP_FUSED | LBM_STEP_MULTIPASS
   long long launches;
 };
 
@@ -69,6 +70,7 @@ struct Ops {
   void (*init)(Handle& h, const double* rho, const double* u, const double* T);
   // one step: pop[cur] -> pop[cur^1] (including the ghost fill)
   void (*step)(Handle& h, const void* src, void* dst);
+  void (*step_multipass)(Handle& h, const void* src, void* dst);
   // macroscopic FP64 fields of pop[cur] into device outputs (any may be NULL);
   // totals (device, D+2 doubles) when non-NULL
   void (*macro)(Handle& h, const void* src, double* rho, double* u, double* T, double* totals);

@@ -2,7 +2,7 @@
 // Each k_*.cu translation unit instantiates one of them.
 #pragma once
 
-#include "lbm_kernels.cuh"
+#include "lbm_fused.cuh"
 
 namespace lbm {
 
@@ -35,7 +35,60 @@ template <int D, typename S, typename real> struct OpsImpl {
     h.launches += 2;
   }
 
+  // tile of the fused kernel: 32 x 8 in-plane nodes in 3-D, 256 x-nodes in 2-D
+  static constexpr int TX = D == 3 ? 32 : 256;
+  static constexpr int TY = D == 3 ? 8 : 1;
+  static constexpr int MINB = sizeof(real) == 8 ? 1 : 2;
+  using FG = FusedGeom<D, TX, TY>;
+
+  struct Launch {
+    int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
+  };
+
+  // One CTA per (column, z-segment); enough segments to fill the resident
+  // CTA slots of the GPU, each at least 16 planes long (6 warm-up planes per
+  // segment), and never more items than slots so that all run together.
+  static Launch plan(const Params& p) {
+    static int blocks_per_sm = -1, sms = 0;
+    const size_t smem = FG::template smem_bytes<real>();
+    if (blocks_per_sm < 0) {
+      auto kern = k_step_fused<D, S, real, TX, TY, MINB>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem);
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    Launch l;
+    l.ncolx = (p.Nx + TX - 1) / TX;
+    l.ncoly = D == 3 ? (p.Ny + TY - 1) / TY : 1;
+    const int Nm = D == 3 ? p.Nz : p.Ny;
+    const long long ncol = (long long)l.ncolx * l.ncoly;
+    const long long slots = (long long)blocks_per_sm * sms;
+    long long nseg = slots / ncol;
+    if (nseg > Nm / 16) nseg = Nm / 16;
+    if (nseg < 1) nseg = 1;
+    l.nseg = int(nseg);
+    long long g = ncol * nseg;
+    if (g > slots) g = slots;
+    l.grid = int(g);
+    return l;
+  }
+
   static void step(Handle& h, const void* src, void* dst) {
+    const Params& p = h.p;
+    const Launch l = plan(p);
+    k_step_fused<D, S, real, TX, TY, MINB><<<l.grid, FG::NT, FG::template smem_bytes<real>(), h.stream>>>(
+        p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst), h.err_dev, l.ncolx, l.ncoly, l.nseg);
+    h.launches += 1;
+    if (!p.periodic_x) {
+      k_ghosts<D, S><<<grid_for(2LL * p.G * p.Ny * p.Nz), kBlock, 0, h.stream>>>(p, reinterpret_cast<ST*>(dst));
+      h.launches += 1;
+    }
+  }
+
+  static void step_multipass(Handle& h, const void* src, void* dst) {
     const Params& p = h.p;
     fields(h, src);
     k_collide<D, S, real><<<grid_for((long long)p.Nx * p.Ny * p.Nz), kBlock, 0, h.stream>>>(
@@ -67,7 +120,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   static size_t scratch_bytes(const Params& p) { return size_t(4 * D + 4) * size_t(p.plane) * sizeof(real); }
 
   static const Ops* ops() {
-    static const Ops o = {&init, &step, &macro};
+    static const Ops o = {&init, &step, &step_multipass, &macro};
     return &o;
   }
 };

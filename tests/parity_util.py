@@ -12,9 +12,9 @@ def oracle_run(case, steps):
     return dict(rho=F["rho"], u=np.stack(F["u"]), T=F["T"], totals=s.totals())
 
 
-def gpu_run(case, steps, precision, chunk=None):
+def gpu_run(case, steps, precision, chunk=None, step_kernel=0):
     import paper_2510_14712_gb300 as P
-    s = P.Solver(case, precision=precision)
+    s = P.Solver(case, precision=precision, step_kernel=step_kernel)
     try:
         s.init()
         if chunk:

@@ -71,6 +71,12 @@ def test_riemann_fp64(riemann_ref):
     assert np.allclose(got["totals"], riemann_ref["totals"], rtol=1e-12, atol=1e-12)
 
 
+def test_riemann_fp64_multipass(riemann_ref):
+    """The multi-pass step kernels reach the same result."""
+    got = gpu_run(inputs.riemann(), 1000, "fp64", step_kernel=P.LBM_STEP_MULTIPASS)
+    assert_parity(got, riemann_ref, 1e-12, "riemann fp64 multipass")
+
+
 def test_riemann_fp32(riemann_ref):
     got = gpu_run(inputs.riemann(), 1000, "fp32")
     assert_parity(got, riemann_ref, 1e-5, "riemann fp32")
@@ -86,6 +92,11 @@ def tgv_ref():
 def test_tgv_d3q27_fp64(tgv_ref):
     got = gpu_run(tgv_case((37, 21, 13)), 100, "fp64")
     assert_parity(got, tgv_ref, 1e-12, "tgv fp64")
+
+
+def test_tgv_d3q27_fp64_multipass(tgv_ref):
+    got = gpu_run(tgv_case((37, 21, 13)), 100, "fp64", step_kernel=P.LBM_STEP_MULTIPASS)
+    assert_parity(got, tgv_ref, 1e-12, "tgv fp64 multipass")
 
 
 def test_tgv_d3q27_fp32(tgv_ref):
