@@ -191,6 +191,35 @@ int lbm_set_step_kernel(lbm_t h, int kind);
 /* Kernel launches enqueued by this handle since creation (for accounting). */
 long long lbm_launch_count(lbm_t h);
 
+/* Conservation totals of caller-provided FP64 device fields, with no memory
+ * allocation of any kind (the paper has no counterpart: this is a service
+ * for callers that cannot allocate).  For example, code that is capturing a
+ * stream into a CUDA graph may not call cudaMalloc; a real-time loop may run
+ * under a fixed device-memory budget; a host framework may route every
+ * allocation through its own pool.  Such callers cannot use a handle (whose
+ * creation allocates) but can still reduce fields they already own.
+ *   lattice: LBM_D2Q9 or LBM_D3Q27 (D = 2 or 3).
+ *   n: number of nodes, 1 <= n <= 67,108,864 (the fixed scratch holds 8192
+ *      blocks of 8192 nodes); larger n is rejected with LBM_EINVAL.
+ *   d_rho, d_T: n doubles; d_u: D planes of n doubles (layout of lbm_moments).
+ *   a, cv: van der Waals a and c_v, for rho E = rho (c_v T - a rho + u^2/2).
+ *   d_totals: device output of D+2 doubles (sum rho, sum rho u_1..u_D,
+ *      sum rho E), the same quantities as the totals of lbm_moments.
+ *   stream: cudaStream_t (as void*) on which the two kernels are enqueued;
+ *      the call returns without waiting.
+ * The block partials live in one file-scope device array of 320 KiB that
+ * every GPU loading the library holds until exit.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All
+ * calls on a device share the array, which keeps the last call's contents;
+ * every call overwrites all the partials it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU race and give wrong totals.
+ * Errors: LBM_EINVAL (bad lattice, NULL pointer, n out of range), LBM_ECUDA;
+ * the message is returned by lbm_totals_noalloc_error(). */
+int lbm_totals_noalloc(int lattice, long long n, const double* d_rho, const double* d_u, const double* d_T,
+                       double a, double cv, double* d_totals, void* stream);
+const char* lbm_totals_noalloc_error(void);
+
 /* Free all resources of the handle.  lbm_destroy(NULL) is a no-op. */
 int lbm_destroy(lbm_t h);
 

@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
 EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
-           "lbm_set_step_kernel", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version")
+           "lbm_set_step_kernel", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version",
+           "lbm_totals_noalloc", "lbm_totals_noalloc_error")
 
 
 class LbmError(RuntimeError):
@@ -81,6 +82,8 @@ def load():
         "lbm_destroy": (I, [P]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
+        "lbm_totals_noalloc": (I, [I, ctypes.c_longlong, P, P, P, D, D, P, P]),
+        "lbm_totals_noalloc_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +212,14 @@ def lbm_launch_count(h):
 def lbm_destroy(h):
     if h:
         load().lbm_destroy(h)
+
+
+def lbm_totals_noalloc(lattice, n, rho, u, T, a, cv, totals, stream_ptr=None):
+    """Totals of device fields into the device tensor ``totals`` without allocating (see include/lbm.h)."""
+    rc = load().lbm_totals_noalloc(lattice, n, _dptr(rho), _dptr(u), _dptr(T), a, cv, _dptr(totals),
+                                   ctypes.c_void_p(stream_ptr) if stream_ptr else None)
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_totals_noalloc_error().decode())
 
 
 def lbm_version():
