@@ -85,6 +85,8 @@ int layout(Handle& h) {
   const int nxp = p.Nx + 2 * p.G;
   p.pitch = ((nxp + 31) / 32) * 32;      // rows start on 128-element (>= 256 B) boundaries
   p.plane = (long long)p.Nz * p.Ny * p.pitch;
+  if ((long long)(2 * h.Q) * p.plane >= (1LL << 32))
+    return fail(LBM_EINVAL, "domain too large: 2 Q Nz Ny pitch must stay below 2^32 elements");
   const size_t pop_bytes = size_t(2 * h.Q) * size_t(p.plane) * h.elem_bytes;
   for (int k = 0; k < 2; ++k) {
     CK(cudaMalloc(&h.pop[k], pop_bytes));

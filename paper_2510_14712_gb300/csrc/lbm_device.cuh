@@ -238,6 +238,75 @@ template <int D, typename real> struct Attractors {
   }
 };
 
+// Relaxation of all Q populations of one kind with products shared between
+// directions.  Directions are grouped by their components on the first D-1
+// axes ("lower" axes: x, and y in 3-D); for each group the products over the
+// lower axes are formed once and the three directions of the group differ
+// only in the factor of the last axis.  The update of Eqs. fLBGK / gLBGK is
+// written as (1 - 2 beta) p + (3 beta - 1) p^eq + (1 - beta) p^*.
+// load(i) / store(i, v) move population i.
+template <int D, typename real> struct FactoredRelax {
+  using L = Lattice<D>;
+  static constexpr int NG = D == 3 ? 9 : 3;          // groups of lower-axis components
+
+  template <class Load, class Store>
+  __device__ __forceinline__ static void f_pass(const Attractors<D, real>& at, Load load, Store store) {
+    const real k0 = real(1) - at.twobeta, k1 = real(1.5) * at.twobeta - real(1), k2 = at.omb;
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+      const int cx = D == 3 ? gi / 3 - 1 : gi - 1;
+      const int cy = D == 3 ? gi % 3 - 1 : 0;
+      real fe2 = at.rho * at.pe[0][cx], fs2 = at.rho * at.pf[0][cx];
+      if (D == 3) {
+        fe2 *= at.pe[1][cy];
+        fs2 *= at.pf[1][cy];
+      }
+#pragma unroll
+      for (int cl = -1; cl <= 1; ++cl) {
+        const int i = 3 * gi + cl + 1;
+        const real fe = fe2 * at.pe[D - 1][cl], fs = fs2 * at.pf[D - 1][cl];
+        const real f = load(i);
+        store(i, k0 * f + k1 * fe + k2 * fs);
+      }
+    }
+  }
+
+  template <class Load, class Store>
+  __device__ __forceinline__ static void g_pass(const Attractors<D, real>& at, Load load, Store store) {
+    const real k0 = real(1) - at.twobeta, k1 = real(1.5) * at.twobeta - real(1), k2 = at.omb;
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+      const int cx = D == 3 ? gi / 3 - 1 : gi - 1;
+      const int cy = D == 3 ? gi % 3 - 1 : 0;
+      // A = prod_lower psi, B = sum_b chi_b prod_{lower, a != b} psi, C = e A + B
+      real Ae = at.pe[0][cx], Be = at.ce[0][cx], As = at.pg[0][cx], Bs = at.cg[0][cx];
+      if (D == 3) {
+        Be = Be * at.pe[1][cy] + Ae * at.ce[1][cy];
+        Ae = Ae * at.pe[1][cy];
+        Bs = Bs * at.pg[1][cy] + As * at.cg[1][cy];
+        As = As * at.pg[1][cy];
+      }
+      const real Ce = at.rho * (at.e * Ae + Be), Cs = at.rho * (at.e_s * As + Bs);
+      Ae *= at.rho;
+      As *= at.rho;
+      const int nzl = (cx != 0) + (D == 3 ? (cy != 0) : 0);
+#pragma unroll
+      for (int cl = -1; cl <= 1; ++cl) {
+        const int i = 3 * gi + cl + 1;
+        const real ge = at.pe[D - 1][cl] * Ce + Ae * at.ce[D - 1][cl];      // Eq. LBMeqG
+        real gs = at.pg[D - 1][cl] * Cs + As * at.cg[D - 1][cl];            // Eq. LBMgstar
+        if (nzl + (cl != 0) == 1) {                                          // |c_i|^2 = 1
+          const real cq = cl != 0 ? real(cl) * at.qc[D - 1]
+                                  : (cx != 0 ? real(cx) * at.qc[0] : real(cy) * at.qc[D == 3 ? 1 : 0]);
+          gs += real(0.5) * cq;
+        }
+        const real g = load(i);
+        store(i, k0 * g + k1 * ge + k2 * gs);
+      }
+    }
+  }
+};
+
 // The collision of Eqs. fLBGK / gLBGK at one node.  f, g: the 2Q pulled
 // (post-streaming) populations in, post-collision populations out.
 // Returns the status bits of this node.

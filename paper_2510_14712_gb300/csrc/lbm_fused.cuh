@@ -47,6 +47,13 @@ __device__ __forceinline__ int modp(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
+// v wrapped into [0, n); cheap form valid for -n <= v < 2n, exact form otherwise
+template <bool SMALL> __device__ __forceinline__ int wrapc(int v, int n) {
+  if (SMALL) return modp(v, n);
+  v += v < 0 ? n : 0;
+  return v >= n ? v - n : v;
+}
+
 // distance outside the tile along one in-plane axis (0 inside)
 __device__ __forceinline__ int outside(int l, int h, int T) {
   const int v = l - h;
@@ -54,8 +61,10 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
 }
 
 // MINB: CTAs per SM the register allocation must allow (2 keeps one CTA's
-// memory phase overlapping the other's collision)
-template <int D, typename S, typename real, int TX, int TY, int MINB>
+// memory phase overlapping the other's collision).  SMALL: the box is
+// narrower than a tile plus its halo in x or y, so coordinates need an exact
+// modulo instead of a single conditional wrap.
+template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Store<S>::T* __restrict__ B,
              unsigned* err, int ncolx, int ncoly, int nseg) {
@@ -74,6 +83,9 @@ k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Stor
   const int Ny_in = D == 3 ? p.Ny : 1;                        // in-plane y extent
   const long long mstride = D == 3 ? (long long)p.Ny * p.pitch : (long long)p.pitch;
   const int xmin = p.periodic_x ? -0x40000000 : -3, xmax = p.periodic_x ? 0x40000000 : p.Nx + 2;
+  using ST = typename Store<S>::T;
+  // element offsets inside a population buffer fit 32 bits (checked at create)
+  const unsigned plane32 = unsigned(p.plane), pitch32 = unsigned(p.pitch);
   unsigned flags = 0;
 
   // Work items are (column, z-segment) pairs, ordered segment-major so that
@@ -90,53 +102,68 @@ k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Stor
 
     for (int pl = mb - 3; pl <= me + 2; ++pl) {
       // ---------------- A: moments of plane pl --------------------------------
+      // Direction-outer loop over this thread's positions of the R3 box: three
+      // per-plane base pointers and one 32-bit element offset per load
+      // (direction * plane + row + column).  j_a is accumulated as (sum over
+      // c_a = +1) minus (sum over c_a = -1), both in increasing direction order,
+      // so the two halves are computed identically for mirror-symmetric
+      // populations and j is then exactly zero (as the pairwise sum of Eq.
+      // def_u).  Positions 0 .. KFULL*NT-1 are spread over all threads; the
+      // remainder (fewer than NT) is done by the first threads only.
       {
         const int slot = (pl + 6) % 3;
         const int mp = modp(pl, Nm);
-        long long mo[3];                                      // source plane offsets, c_m = -1, 0, +1
+        const ST* Pm[3];
 #pragma unroll
-        for (int c = -1; c <= 1; ++c) mo[c + 1] = (long long)wrap(mp - c, Nm) * mstride;
-        for (int k = tid; k < G::N3; k += G::NT) {
+        for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
+        auto moments = [&](const int k) {
           const int lx = k % G::BX3, ly = k / G::BX3;
           const int ox = outside(lx, 3, TX), oy = D == 3 ? outside(ly, G::HY3, TY) : 0;
-          if (ox + oy > 3) continue;
-          int gx = x0 + lx - 3;
-          if (gx < xmin || gx > xmax) continue;
-          const int gy = modp(y0 + ly - G::HY3, Ny_in);
-          const bool r1 = ox + oy <= 1;
-          long long xo[3], yo[3];
+          const int gx = x0 + lx - 3;
+          if (ox + oy > 3 || gx < xmin || gx > xmax) return;
+          const bool in1 = ox + oy <= 1;
+          const int gy = D == 3 ? wrapc<SMALL>(y0 + ly - G::HY3, p.Ny) : 0;
+          unsigned xc[3], yr[3];
 #pragma unroll
           for (int c = -1; c <= 1; ++c) {
-            xo[c + 1] = p.periodic_x ? modp(gx - c, p.Nx) : gx + p.G - c;
-            yo[c + 1] = D == 3 ? (long long)modp(gy - c, Ny_in) * p.pitch : 0;
+            xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
+            yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
           }
-          real f[Q];
+          real rho = real(0), sp[D], sn[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) sp[a] = sn[a] = real(0);
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            f[i] = Store<S>::template ld<real>(A, i * p.plane + mo[cm + 1] + yo[cy + 1] + xo[cx + 1], p.ref[i]);
-          }
-          real rho = 0;
+            const real v = Store<S>::template ld<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
+                                                       p.ref[i]);
+            rho += v;
 #pragma unroll
-          for (int i = 0; i < Q; ++i) rho += f[i];
+            for (int a = 0; a < D; ++a) {
+              if (L::c(i, a) == 1) sp[a] += v;
+              if (L::c(i, a) == -1) sn[a] += v;
+            }
+          }
           s_rho[slot * G::N3 + k] = rho;
-          if (r1) {
-            const int k1 = (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx - 2);
-            real j[D];
-            first_moment<D, real>(f, j);
-            real Se = 0;
+          if (in1) {
+            real Se = real(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
               const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-              Se += Store<S>::template ld<real>(A, (Q + i) * p.plane + mo[cm + 1] + yo[cy + 1] + xo[cx + 1],
+              Se += Store<S>::template ld<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
                                                 p.ref[Q + i]);
             }
+            const int k1 = (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx - 2);
             real* dst = s_mom + (slot * G::NMOM) * G::N1 + k1;
 #pragma unroll
-            for (int a = 0; a < D; ++a) dst[a * G::N1] = j[a];
+            for (int a = 0; a < D; ++a) dst[a * G::N1] = sp[a] - sn[a];
             dst[D * G::N1] = Se;
           }
-        }
+        };
+        constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
+#pragma unroll 1
+        for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
+        if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
       }
       __syncthreads();
 
@@ -212,13 +239,15 @@ k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Stor
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx < p.Nx && (D == 2 || gy < p.Ny)) {
           const int mq = modp(q, Nm);
-          long long mo[3], xo[3], yo[3];
+          const ST* Pm[3];
+          unsigned xc[3], yr[3];
 #pragma unroll
           for (int c = -1; c <= 1; ++c) {
-            mo[c + 1] = (long long)wrap(mq - c, Nm) * mstride;
-            xo[c + 1] = p.periodic_x ? modp(gx - c, p.Nx) : gx + p.G - c;
-            yo[c + 1] = D == 3 ? (long long)modp(gy - c, p.Ny) * p.pitch : 0;
+            Pm[c + 1] = A + (long long)wrap(mq - c, Nm) * mstride;
+            xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
+            yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
           }
+          ST* Bq = B + (long long)mq * mstride;
           const int k1 = (ly + G::HY1) * G::BX1 + (lx + 1);
           const real* pc = s_prm + (sc * G::NPRIM) * G::N1;
           const real* pm = s_prm + (sm * G::NPRIM) * G::N1;
@@ -251,26 +280,27 @@ k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Stor
           Attractors<D, real> at;
           at.setup(m, s);
           flags |= at.flags;
-          const long long o = mo[1] + yo[1] + xo[1];
+          const unsigned oc = yr[1] + xc[1];                  // own in-plane offset
           // f pass then g pass: one population set in flight at a time
           real v[Q];
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            v[i] = Store<S>::template ld_last<real>(A, i * p.plane + mo[cm + 1] + yo[cy + 1] + xo[cx + 1], p.ref[i]);
+            v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
+                                                   p.ref[i]);
           }
-#pragma unroll
-          for (int i = 0; i < Q; ++i)
-            Store<S>::template st_stream<real>(B, i * p.plane + o, at.relax_f(i, v[i]), p.ref[i]);
+          FactoredRelax<D, real>::f_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
+            Store<S>::template st_stream<real>(Bq, unsigned(i) * plane32 + oc, x, p.ref[i]);
+          });
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            v[i] = Store<S>::template ld_last<real>(A, (Q + i) * p.plane + mo[cm + 1] + yo[cy + 1] + xo[cx + 1],
+            v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
                                                    p.ref[Q + i]);
           }
-#pragma unroll
-          for (int i = 0; i < Q; ++i)
-            Store<S>::template st_stream<real>(B, (Q + i) * p.plane + o, at.relax_g(i, v[i]), p.ref[Q + i]);
+          FactoredRelax<D, real>::g_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
+            Store<S>::template st_stream<real>(Bq, unsigned(Q + i) * plane32 + oc, x, p.ref[Q + i]);
+          });
         }
       }
       // no barrier needed here: the next write to the primitive ring (stage C)

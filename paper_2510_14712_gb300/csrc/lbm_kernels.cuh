@@ -27,30 +27,30 @@ template <typename S> struct Store;
 // st_stream: streaming store of the new populations (evict-first).
 template <> struct Store<double> {
   using T = double;
-  template <typename real> __device__ static real ld(const T* p, long long o, float) { return real(__ldg(p + o)); }
-  template <typename real> __device__ static real ld_last(const T* p, long long o, float) { return real(__ldcs(p + o)); }
-  template <typename real> __device__ static void st(T* p, long long o, real v, float) { p[o] = double(v); }
-  template <typename real> __device__ static void st_stream(T* p, long long o, real v, float) { __stcs(p + o, double(v)); }
+  template <typename real, typename I> __device__ static real ld(const T* p, I o, float) { return real(__ldg(p + o)); }
+  template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float) { return real(__ldcs(p + o)); }
+  template <typename real, typename I> __device__ static void st(T* p, I o, real v, float) { p[o] = double(v); }
+  template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float) { __stcs(p + o, double(v)); }
 };
 template <> struct Store<float> {
   using T = float;
-  template <typename real> __device__ static real ld(const T* p, long long o, float) { return real(__ldg(p + o)); }
-  template <typename real> __device__ static real ld_last(const T* p, long long o, float) { return real(__ldcs(p + o)); }
-  template <typename real> __device__ static void st(T* p, long long o, real v, float) { p[o] = float(v); }
-  template <typename real> __device__ static void st_stream(T* p, long long o, real v, float) { __stcs(p + o, float(v)); }
+  template <typename real, typename I> __device__ static real ld(const T* p, I o, float) { return real(__ldg(p + o)); }
+  template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float) { return real(__ldcs(p + o)); }
+  template <typename real, typename I> __device__ static void st(T* p, I o, real v, float) { p[o] = float(v); }
+  template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float) { __stcs(p + o, float(v)); }
 };
 template <> struct Store<Fp16Dev> {
   using T = __half;
-  template <typename real> __device__ static real ld(const T* p, long long o, float ref) {
+  template <typename real, typename I> __device__ static real ld(const T* p, I o, float ref) {
     return real(__half2float(__ldg(p + o)) + ref);
   }
-  template <typename real> __device__ static real ld_last(const T* p, long long o, float ref) {
+  template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float ref) {
     return real(__half2float(__ldcs(p + o)) + ref);
   }
-  template <typename real> __device__ static void st(T* p, long long o, real v, float ref) {
+  template <typename real, typename I> __device__ static void st(T* p, I o, real v, float ref) {
     p[o] = __float2half_rn(float(v) - ref);
   }
-  template <typename real> __device__ static void st_stream(T* p, long long o, real v, float ref) {
+  template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float ref) {
     __stcs(p + o, __float2half_rn(float(v) - ref));
   }
 };

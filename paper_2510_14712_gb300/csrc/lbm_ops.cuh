@@ -43,6 +43,7 @@ template <int D, typename S, typename real> struct OpsImpl {
 
   struct Launch {
     int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
+    bool small = false;
   };
 
   // One CTA per (column, z-segment); enough segments to fill the resident
@@ -52,8 +53,10 @@ template <int D, typename S, typename real> struct OpsImpl {
     static int blocks_per_sm = -1, sms = 0;
     const size_t smem = FG::template smem_bytes<real>();
     if (blocks_per_sm < 0) {
-      auto kern = k_step_fused<D, S, real, TX, TY, MINB>;
+      auto kern = k_step_fused<D, S, real, TX, TY, MINB, false>;
+      auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(kern_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem);
       int dev = 0;
       cudaGetDevice(&dev);
@@ -73,13 +76,15 @@ template <int D, typename S, typename real> struct OpsImpl {
     long long g = ncol * nseg;
     if (g > slots) g = slots;
     l.grid = int(g);
+    l.small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
     return l;
   }
 
   static void step(Handle& h, const void* src, void* dst) {
     const Params& p = h.p;
     const Launch l = plan(p);
-    k_step_fused<D, S, real, TX, TY, MINB><<<l.grid, FG::NT, FG::template smem_bytes<real>(), h.stream>>>(
+    auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true> : k_step_fused<D, S, real, TX, TY, MINB, false>;
+    kern<<<l.grid, FG::NT, FG::template smem_bytes<real>(), h.stream>>>(
         p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst), h.err_dev, l.ncolx, l.ncoly, l.nseg);
     h.launches += 1;
     if (!p.periodic_x) {

@@ -48,6 +48,14 @@ def tgv_case(shape, nu=0.02, seed=0, drift=None):
 
 DRIFT = (0.08, -0.05, 0.06)
 
+# FP32 bound for the shock-carrying D2Q9 cases, derived from the arithmetic.
+# Shocks and contacts amplify rounding: over 1000 steps of the Riemann
+# problem the FP64 build differs from the FP64 oracle by 2.9e-14 in u from a
+# unit roundoff of 1.1e-16, a gain of about 2.6e2.  The same gain applied to
+# FP32's 6e-8 gives 1.6e-5, so 1e-5 is out of reach there; the bound is 5e-5
+# (3x margin).  The 1e-5 FP32 bound holds for the smooth Taylor-Green cases.
+FP32_SHOCK_TOL = 5e-5
+
 
 def shock_case(Nx=400, Ny=3, Ma=1.2):
     from oracle import thermo
@@ -79,7 +87,7 @@ def test_riemann_fp64_multipass(riemann_ref):
 
 def test_riemann_fp32(riemann_ref):
     got = gpu_run(inputs.riemann(), 1000, "fp32")
-    assert_parity(got, riemann_ref, 1e-5, "riemann fp32")
+    assert_parity(got, riemann_ref, FP32_SHOCK_TOL, "riemann fp32")
 
 
 # ---- D3Q27 Taylor-Green with noise on a ragged box -------------------------------
@@ -121,7 +129,7 @@ def test_tgv_d3q27_fp32_long(tgv_long_ref):
 
 # ---- D2Q9 shock tube with inflow / outflow faces ---------------------------------
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", FP32_SHOCK_TOL)])
 def test_shock_tube(precision, tol):
     want = oracle_run(shock_case(), 300)
     got = gpu_run(shock_case(), 300, precision)
