@@ -217,6 +217,9 @@ def run_ours(args):
     u = torch.from_numpy(np.ascontiguousarray(np.stack(case.u), dtype=np.float64)).to(dev)
     T = torch.from_numpy(np.ascontiguousarray(case.T, dtype=np.float64)).to(dev)
     P.lbm_init_device(solver.h, rho, u, T)
+    tile = None
+    if sk == P.LBM_STEP_FUSED and not args.no_autotune:
+        tile = P.lbm_autotune(solver.h, 3)
 
     # warm-up
     P.lbm_step(solver.h, args.warmup)
@@ -298,6 +301,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
             "config": {"workload": desc, "nodes": N, "lattice": "D%dQ%d" % (case.D, Q), "precision": prec,
                        "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "tile_shape": tile[0] if tile else None,
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -323,6 +327,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp16dev"])
     ap.add_argument("--step-kernel", default="fused", choices=["fused", "multipass"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -188,6 +188,15 @@ enum { LBM_STEP_FUSED = 0, LBM_STEP_MULTIPASS = 1 };
  * Errors: LBM_EINVAL (NULL handle or unknown kind). */
 int lbm_set_step_kernel(lbm_t h, int kind);
 
+/* Time each tile shape of the fused step kernel for `reps` steps from the
+ * current state (writing only the spare buffer: the state does not advance)
+ * and use the fastest from then on.  *chosen (may be NULL) receives the index
+ * of the shape (0 is the default), *ms_per_step (may be NULL) its time.
+ * The choice is remembered for the process: a later lbm_init of any handle
+ * with the same lattice, precision, size and x boundary type uses it.
+ * Synchronises.  Errors: LBM_EINVAL, LBM_ESTATE (before lbm_init), LBM_ECUDA. */
+int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step);
+
 /* Kernel launches enqueued by this handle since creation (for accounting). */
 long long lbm_launch_count(lbm_t h);
 

@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
 EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
-           "lbm_set_step_kernel", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version",
+           "lbm_set_step_kernel", "lbm_autotune", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version",
            "lbm_totals_noalloc", "lbm_totals_noalloc_error")
 
 
@@ -78,6 +78,7 @@ def load():
         "lbm_get_populations": (I, [P, P, S]),
         "lbm_set_populations": (I, [P, P, S]),
         "lbm_set_step_kernel": (I, [P, I]),
+        "lbm_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]),
         "lbm_launch_count": (ctypes.c_longlong, [P]),
         "lbm_destroy": (I, [P]),
         "lbm_last_error": (ctypes.c_char_p, []),
@@ -203,6 +204,13 @@ def lbm_set_populations(h, buf):
 
 def lbm_set_step_kernel(h, kind):
     _check(load().lbm_set_step_kernel(h, kind))
+
+
+def lbm_autotune(h, reps=3):
+    """Pick the fastest fused-kernel tile shape; returns (index, ms per step)."""
+    c, ms = ctypes.c_int(), ctypes.c_float()
+    _check(load().lbm_autotune(h, reps, ctypes.byref(c), ctypes.byref(ms)))
+    return c.value, ms.value
 
 
 def lbm_launch_count(h):

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -113,6 +114,39 @@ void set_face_eq(Handle& h, int face) {
     eq[i] = feq[i];
     eq[h.Q + i] = geq[i];
   }
+}
+
+// Autotune results of this process, keyed by lattice, precision and padded
+// geometry: a new handle of the same shape starts with the tuned tile.
+struct TuneEntry {
+  int Q, precision, Nx, Ny, Nz, periodic_x, cfg;
+};
+TuneEntry g_tuned[32];
+int g_ntuned = 0;
+std::mutex g_tune_mu;
+
+int tuned_cfg(const Handle& h) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int k = 0; k < g_ntuned; ++k) {
+    const TuneEntry& e = g_tuned[k];
+    if (e.Q == h.Q && e.precision == h.precision && e.Nx == h.Nx && e.Ny == h.Ny && e.Nz == h.Nz &&
+        e.periodic_x == h.p.periodic_x)
+      return e.cfg;
+  }
+  return 0;
+}
+
+void remember_cfg(const Handle& h) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int k = 0; k < g_ntuned; ++k) {
+    TuneEntry& e = g_tuned[k];
+    if (e.Q == h.Q && e.precision == h.precision && e.Nx == h.Nx && e.Ny == h.Ny && e.Nz == h.Nz &&
+        e.periodic_x == h.p.periodic_x) {
+      e.cfg = h.tile_cfg;
+      return;
+    }
+  }
+  if (g_ntuned < 32) g_tuned[g_ntuned++] = {h.Q, h.precision, h.Nx, h.Ny, h.Nz, h.p.periodic_x, h.tile_cfg};
 }
 
 int read_err(Handle& h) {
@@ -245,6 +279,7 @@ int lbm_set_stream(lbm_t h, void* stream) {
 static int init_common(lbm_t h, const double* d_rho, const double* d_u, const double* d_T) {
   CK(cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream));
   h->cur = 0;
+  h->tile_cfg = tuned_cfg(*h);
   ops_for(*h)->init(*h, d_rho, d_u, d_T);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
@@ -356,6 +391,18 @@ int lbm_set_step_kernel(lbm_t h, int kind) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (kind != LBM_STEP_FUSED && kind != LBM_STEP_MULTIPASS) return fail(LBM_EINVAL, "unknown step kernel");
   h->step_kernel = kind;
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!h->initialized) return fail(LBM_ESTATE, "lbm_init has not been called");
+  if (reps < 1) return fail(LBM_EINVAL, "reps must be >= 1");
+  const int c = ops_for(*h)->autotune(*h, reps, ms_per_step);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  remember_cfg(*h);
+  if (chosen) *chosen = c;
   return LBM_OK;
 }
 

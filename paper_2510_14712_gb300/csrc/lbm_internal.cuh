@@ -61,6 +61,7 @@ struct Handle {
   cudaStream_t stream;
   int initialized, unstable;
   int step_kernel;            // LBM_STEP_FUSED | LBM_STEP_MULTIPASS
+  int tile_cfg;               // index of the fused kernel's tile shape (lbm_autotune)
   long long launches;
 };
 
@@ -74,6 +75,8 @@ struct Ops {
   // macroscopic FP64 fields of pop[cur] into device outputs (any may be NULL);
   // totals (device, D+2 doubles) when non-NULL
   void (*macro)(Handle& h, const void* src, double* rho, double* u, double* T, double* totals);
+  // time the fused kernel's tile shapes, keep the fastest; returns its index
+  int (*autotune)(Handle& h, int reps, float* best_ms);
 };
 
 const Ops* ops_d2_fp64();

@@ -35,62 +35,121 @@ template <int D, typename S, typename real> struct OpsImpl {
     h.launches += 2;
   }
 
-  // tile of the fused kernel: 32 x 8 in-plane nodes in 3-D, 256 x-nodes in 2-D
-  static constexpr int TX = D == 3 ? 32 : 256;
-  static constexpr int TY = D == 3 ? 8 : 1;
-  static constexpr int MINB = sizeof(real) == 8 ? 1 : 2;
-  using FG = FusedGeom<D, TX, TY>;
-
-  struct Launch {
-    int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
-    bool small = false;
+  // One tile shape of the fused kernel (TX x TY in-plane nodes, MINB CTAs
+  // per SM for the register budget).
+  template <int TX, int TY, int MINB> struct Fused {
+    using FG = FusedGeom<D, TX, TY>;
+    struct Launch {
+      int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
+      bool small = false;
+    };
+    // One CTA per (column, z-segment); enough segments to fill the resident
+    // CTA slots of the GPU, each at least 16 planes long (6 warm-up planes per
+    // segment), and never more items than slots so that all run together.
+    static Launch plan(const Params& p) {
+      static int blocks_per_sm = -1, sms = 0;
+      const size_t smem = FG::template smem_bytes<real>();
+      if (blocks_per_sm < 0) {
+        auto kern = k_step_fused<D, S, real, TX, TY, MINB, false>;
+        auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaFuncSetAttribute(kern_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+      }
+      Launch l;
+      l.ncolx = (p.Nx + TX - 1) / TX;
+      l.ncoly = D == 3 ? (p.Ny + TY - 1) / TY : 1;
+      const int Nm = D == 3 ? p.Nz : p.Ny;
+      const long long ncol = (long long)l.ncolx * l.ncoly;
+      const long long slots = (long long)blocks_per_sm * sms;
+      long long nseg = slots / ncol;
+      if (nseg > Nm / 16) nseg = Nm / 16;
+      if (nseg < 1) nseg = 1;
+      l.nseg = int(nseg);
+      long long g = ncol * nseg;
+      if (g > slots) g = slots;
+      l.grid = int(g);
+      l.small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
+      return l;
+    }
+    static void launch(Handle& h, const void* src, void* dst) {
+      const Params& p = h.p;
+      const Launch l = plan(p);
+      auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true> : k_step_fused<D, S, real, TX, TY, MINB, false>;
+      kern<<<l.grid, FG::NT, FG::template smem_bytes<real>(), h.stream>>>(
+          p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst), h.err_dev, l.ncolx, l.ncoly, l.nseg);
+      h.launches += 1;
+    }
   };
 
-  // One CTA per (column, z-segment); enough segments to fill the resident
-  // CTA slots of the GPU, each at least 16 planes long (6 warm-up planes per
-  // segment), and never more items than slots so that all run together.
-  static Launch plan(const Params& p) {
-    static int blocks_per_sm = -1, sms = 0;
-    const size_t smem = FG::template smem_bytes<real>();
-    if (blocks_per_sm < 0) {
-      auto kern = k_step_fused<D, S, real, TX, TY, MINB, false>;
-      auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true>;
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      cudaFuncSetAttribute(kern_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem);
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
+  // Candidate tile shapes, first = default.  FP64 keeps one shape (its
+  // arithmetic, not the tile, bounds it).
+  using LaunchFn = void (*)(Handle&, const void*, void*);
+  static int candidates(const LaunchFn** fns) {
+    if (D == 3) {
+      if (sizeof(real) == 8) {
+        static const LaunchFn c[] = {&Fused<32, 8, 1>::launch};
+        *fns = c;
+        return 1;
+      }
+      static const LaunchFn c[] = {&Fused<32, 8, 2>::launch, &Fused<32, 16, 1>::launch, &Fused<16, 16, 2>::launch};
+      *fns = c;
+      return 3;
     }
-    Launch l;
-    l.ncolx = (p.Nx + TX - 1) / TX;
-    l.ncoly = D == 3 ? (p.Ny + TY - 1) / TY : 1;
-    const int Nm = D == 3 ? p.Nz : p.Ny;
-    const long long ncol = (long long)l.ncolx * l.ncoly;
-    const long long slots = (long long)blocks_per_sm * sms;
-    long long nseg = slots / ncol;
-    if (nseg > Nm / 16) nseg = Nm / 16;
-    if (nseg < 1) nseg = 1;
-    l.nseg = int(nseg);
-    long long g = ncol * nseg;
-    if (g > slots) g = slots;
-    l.grid = int(g);
-    l.small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
-    return l;
+    static const LaunchFn c[] = {&Fused<256, 1, 2>::launch, &Fused<128, 1, 4>::launch, &Fused<512, 1, 1>::launch};
+    *fns = c;
+    return 3;
   }
 
-  static void step(Handle& h, const void* src, void* dst) {
+  static void ghosts(Handle& h, void* dst) {
     const Params& p = h.p;
-    const Launch l = plan(p);
-    auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true> : k_step_fused<D, S, real, TX, TY, MINB, false>;
-    kern<<<l.grid, FG::NT, FG::template smem_bytes<real>(), h.stream>>>(
-        p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst), h.err_dev, l.ncolx, l.ncoly, l.nseg);
-    h.launches += 1;
     if (!p.periodic_x) {
       k_ghosts<D, S><<<grid_for(2LL * p.G * p.Ny * p.Nz), kBlock, 0, h.stream>>>(p, reinterpret_cast<ST*>(dst));
       h.launches += 1;
     }
+  }
+
+  static void step(Handle& h, const void* src, void* dst) {
+    const LaunchFn* fns;
+    const int n = candidates(&fns);
+    fns[h.tile_cfg < n ? h.tile_cfg : 0](h, src, dst);
+    ghosts(h, dst);
+  }
+
+  // Time every candidate shape for `reps` steps from the current state into
+  // the spare buffer (the state is not advanced) and keep the fastest.
+  static int autotune(Handle& h, int reps, float* best_ms) {
+    const LaunchFn* fns;
+    const int n = candidates(&fns);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float bt = 1e30f;
+    const void* src = h.pop[h.cur];
+    void* dst = h.pop[h.cur ^ 1];
+    for (int c = 0; c < n; ++c) {
+      fns[c](h, src, dst);                                   // warm-up / occupancy query
+      cudaEventRecord(e0, h.stream);
+      for (int r = 0; r < reps; ++r) fns[c](h, src, dst);
+      cudaEventRecord(e1, h.stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < bt) {
+        bt = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h.tile_cfg = best;
+    if (best_ms) *best_ms = bt / (reps > 0 ? reps : 1);
+    return best;
   }
 
   static void step_multipass(Handle& h, const void* src, void* dst) {
@@ -125,7 +184,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   static size_t scratch_bytes(const Params& p) { return size_t(4 * D + 4) * size_t(p.plane) * sizeof(real); }
 
   static const Ops* ops() {
-    static const Ops o = {&init, &step, &step_multipass, &macro};
+    static const Ops o = {&init, &step, &step_multipass, &macro, &autotune};
     return &o;
   }
 };
