@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # name: (builder kwargs, precision, description)
     "tgv256": ("tgv", dict(N=256), "fp32", "D3Q27 compressible Taylor-Green vortex 256^3, vdW dense vapour, FP32"),
+    "tgv128": ("tgv", dict(N=128), "fp32", "D3Q27 Taylor-Green 128^3, FP32 (small profiling case)"),
     "tgv256-fp64": ("tgv", dict(N=256), "fp64", "D3Q27 compressible Taylor-Green vortex 256^3, FP64"),
     "tgv256-fp16dev": ("tgv", dict(N=256), "fp16dev", "D3Q27 Taylor-Green 256^3, FP16-deviation storage"),
     "riemann": ("riemann", dict(), "fp64", "D2Q9 non-ideal Riemann problem 1000x4, FP64"),

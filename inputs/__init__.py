@@ -147,10 +147,13 @@ def tgv(N=256, shape=None):
     u = U0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0), k = 2 pi / N per
     axis; T = T0 + T_amp (cos 2kx + cos 2ky)(cos 2kz + 2), the temperature that
     gives the classical TGV pressure at constant density (T_amp stored).
+    The stored relaxation time is for the 256-node box; at fixed Reynolds
+    number it scales with the box length in nodes (taken along x).
     """
     sc = scenario("tgv_d3q27")
     shape = (N, N, N) if shape is None else tuple(shape)
     c = _base("tgv_d3q27", sc, shape)
+    c.tau = sc["tau"] * shape[0] / sc["N"]
     x, y, z = c.grid()
     kx, ky, kz = (2 * np.pi / n for n in shape)
     U0 = sc["U0"]

@@ -10,8 +10,10 @@ P_c = 1, so R = 8/3, a = 3, b = 1/3; c_v/R = 3).  The lattice scheme is stable
 only for theta = P/rho < 1/3 (Sec. 5), so velocities are rescaled by U: lattice
 u = u_r / U, T = T_r / U^2, a = a_r / U^2, with rho, b, R, c_v unchanged.  U^2 is
 the smallest integer with max(theta_r)/U^2 <= 1/4 over the states of the
-workload.  Viscosities nu are lattice values; mu = nu rho_ref and the stored
-relaxation time is tau = mu / P(rho_ref, T_ref) (Sec. 3.1, tau = mu/P).
+workload.  Viscosities of the D2Q9 workloads are lattice values (their boxes
+fix no reduced length); the Taylor-Green viscosity is a reduced value on the
+[0, 2 pi)^3 box (see tgv).  mu = nu rho_ref and the stored relaxation time is
+tau = mu / P(rho_ref, T_ref) (Sec. 3.1, tau = mu/P).
 """
 import json
 import math
@@ -70,8 +72,15 @@ def _shock_drop(D, Ma, nu):
                 shock_speed=us / U)
 
 
-def tgv():
-    """D3Q27 compressible Taylor-Green vortex in dense vapour (rho0=0.6, T0=1.05, Ma 0.5)."""
+def tgv(N=256, nu_reduced=1e-3):
+    """D3Q27 compressible Taylor-Green vortex in dense vapour (rho0=0.6, T0=1.05, Ma 0.5).
+
+    nu = 1e-3 is a reduced-unit viscosity like rho0 and T0, on the classic
+    Taylor-Green box [0, 2 pi)^3: one lattice spacing is 2 pi / N reduced
+    lengths and one lattice velocity unit is U reduced velocities, so
+    nu_lattice = nu_reduced / (U 2 pi / N); Re = U0_r / nu_r = 747.  tau is
+    stored for N = 256 and scales linearly with N at fixed Re.
+    """
     rho0, T0 = 0.6, 1.05
     U2 = _u2_for([(rho0, T0)])
     eos = _lattice_eos(U2, kappa=0.01, eta_over_mu=1.0, rho_ref=rho0, T_ref_r=T0)
@@ -80,8 +89,10 @@ def tgv():
     # T from Eq. Pvdw at constant rho0 is affine in P:
     #   T = T0 + dP (1 - b rho0)/(rho0 R),  dP = rho0 U0^2/16 (cos2x + cos2y)(cos2z + 2)
     T_amp = U0 * U0 * (1.0 - B * rho0) / (16.0 * R_GAS)
-    return dict(D=3, U2=U2, cv=CV, Pr=0.71, nu=1e-3, eos=eos, tau=_tau(eos, 1e-3),
-                rho0=rho0, T0=T0 / U2, U0=U0, T_amp=T_amp, cs=cs)
+    nu_lat = nu_reduced / (math.sqrt(U2) * 2.0 * math.pi / N)
+    return dict(D=3, U2=U2, cv=CV, Pr=0.71, nu_reduced=nu_reduced, N=N, nu=nu_lat, eos=eos,
+                tau=_tau(eos, nu_lat), rho0=rho0, T0=T0 / U2, U0=U0, T_amp=T_amp, cs=cs,
+                Re=0.5 * math.sqrt(thermo.sound_speed_sq(rho0, T0, A_R, B, R_GAS, CV)) / nu_reduced)
 
 
 def main():

@@ -40,7 +40,7 @@ def tgv_case(shape, nu=0.02, seed=0, drift=None):
     """
     c = inputs.add_noise(inputs.tgv(shape=shape), seed)
     sc = inputs.scenario("tgv_d3q27")
-    c.tau = sc["tau"] * nu / sc["nu"]
+    c.tau = sc["tau"] * nu / sc["nu"]          # lattice viscosity nu (tau is linear in nu)
     if drift is not None:
         c.u = [ua + d for ua, d in zip(c.u, drift)]
     return c
