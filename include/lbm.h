@@ -200,6 +200,54 @@ int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step);
 /* Kernel launches enqueued by this handle since creation (for accounting). */
 long long lbm_launch_count(lbm_t h);
 
+/* ---- batches ------------------------------------------------------------
+ * Many independent instances of one lattice, fluid and precision, each with
+ * its own size and x faces, advanced together: every step is one launch of a
+ * persistent fused kernel over a work list of (instance, column, plane range)
+ * items sorted longest first and taken from an atomic counter, followed by one
+ * batched ghost fill; the two launches of a step are captured in a CUDA graph
+ * (one per buffer parity).  Results are bit-identical to stepping each
+ * instance alone.  Instances are numbered 0..n-1; all per-instance calls take
+ * that index.  The batch uses its own non-blocking stream unless
+ * lbm_batch_set_stream gives one (the default stream cannot be captured). */
+typedef struct lbm_batch_s* lbm_batch_t;
+
+/* n instances of sizes Nx[k] x Ny[k] (x Nz[k] for D3Q27; Nz may be NULL for
+ * D2Q9); eos, tau, Pr, cv as for lbm_create, shared by all instances.
+ * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA (message: lbm_batch_last_error). */
+int lbm_batch_create(lbm_batch_t* out, int lattice, int n, const int* Nx, const int* Ny, const int* Nz,
+                     const lbm_eos* eos, double tau, double Pr, double cv);
+/* lbm_set_boundary for instance k. */
+int lbm_batch_set_boundary(lbm_batch_t b, int k, int face, int type, const double* state);
+/* Use a caller stream (non-NULL) instead of the batch's own. */
+int lbm_batch_set_stream(lbm_batch_t b, void* stream);
+/* lbm_init for instance k (host arrays); may be called at any step. */
+int lbm_batch_init(lbm_batch_t b, int k, const double* rho, const double* u, const double* T);
+/* Advance every instance n steps (n graph launches), then read the status
+ * words of all instances.  Errors: LBM_ESTATE (an instance not initialised,
+ * or unstable since its last init), LBM_EUNSTABLE, LBM_EINVAL, LBM_ECUDA. */
+int lbm_batch_step(lbm_batch_t b, int n);
+/* Same without the status read (no synchronisation). */
+int lbm_batch_step_async(lbm_batch_t b, int n);
+/* Wait for the batch stream and report the status words as lbm_batch_step. */
+int lbm_batch_sync(lbm_batch_t b);
+/* lbm_moments for instance k. */
+int lbm_batch_moments(lbm_batch_t b, int k, double* rho, double* u, double* T, double* totals);
+/* Status bits (LBM_FLAG_*) of instance k since its last init. */
+int lbm_batch_flags(lbm_batch_t b, int k, unsigned* flags);
+/* Time each tile shape of the batched kernel for `reps` steps from the
+ * current state (spare buffers only; the state does not advance) and keep the
+ * fastest.  *chosen and *ms_per_step may be NULL. */
+int lbm_batch_autotune(lbm_batch_t b, int reps, int* chosen, float* ms_per_step);
+/* Interior nodes summed over the instances. */
+long long lbm_batch_nodes(lbm_batch_t b);
+/* Kernel launches enqueued by the batch's steps (2 per step). */
+long long lbm_batch_launch_count(lbm_batch_t b);
+/* Free the batch and all its instances.  lbm_batch_destroy(NULL) is a no-op. */
+int lbm_batch_destroy(lbm_batch_t b);
+/* Message of the last failed lbm_batch_* call on this thread. */
+const char* lbm_batch_last_error(void);
+
 /* Conservation totals of caller-provided FP64 device fields, with no memory
  * allocation of any kind (the paper has no counterpart: this is a service
  * for callers that cannot allocate).  For example, code that is capturing a

@@ -165,6 +165,25 @@ def tgv(N=256, shape=None):
     return c
 
 
+def batch(n=None):
+    """The uneven D2Q9 shock-tube instances of the batched workload.
+
+    Sizes, shock positions and post-shock states come from the stored table;
+    each instance is a shock tube with equilibrium inflow at x = 0 and a
+    zero-gradient outflow at x = Nx - 1.
+    """
+    tab = scenario("batch_d2q9")
+    base = scenario(tab["base"])
+    cases = []
+    for d in tab["instances"][:n]:
+        sc = dict(base)
+        sc["post"] = d["post"]
+        c = shock_drop(2, (d["Nx"], d["Ny"]), shock_x=d["shock_x"], with_drop=False, sc=sc)
+        c.name = tab["base"]
+        cases.append(c)
+    return cases
+
+
 def add_noise(c, seed, rel=1e-3):
     """Seeded perturbation: rho *= 1 + rel U, u += rel c_ref U (U in [-1,1)).
 

@@ -95,6 +95,32 @@ def tgv(N=256, nu_reduced=1e-3):
                 Re=0.5 * math.sqrt(thermo.sound_speed_sq(rho0, T0, A_R, B, R_GAS, CV)) / nu_reduced)
 
 
+def batch(n=256, seed=2025, Ma_lo=1.1, Ma_hi=1.3):
+    """Uneven D2Q9 shock-tube instances for the batched form.
+
+    Nx uniform over the multiples of 64 in [128, 1024], Ny = Nx/2, shock Mach
+    number uniform in [Ma_lo, Ma_hi], shock at x = Nx/8, vapour at rest ahead
+    of it.  Draws come from the seeded generator of inputs/ (two streams);
+    each Rankine-Hugoniot post-state is computed here.  Ma is capped at 1.3
+    and no drop is placed: larger Ma and liquid drops need the shock-capturing
+    viscosity of Sec. 4.4, which this build does not have.
+    """
+    import inputs
+    sd = _shock_drop(2, 1.2, 0.01)
+    vap = (0.3, 1.1)
+    U = math.sqrt(sd["U2"])
+    kx = inputs.uniform(seed, n)
+    km = inputs.uniform(seed + 1, n)
+    out = []
+    for k in range(n):
+        nx = 64 * (2 + min(14, int((kx[k] + 1.0) * 0.5 * 15)))
+        Ma = Ma_lo + (Ma_hi - Ma_lo) * (km[k] + 1.0) * 0.5
+        r2, T2, u2, us = thermo.rankine_hugoniot(vap[0], vap[1], 0.0, Ma, A_R, B, R_GAS, CV)
+        out.append(dict(Nx=nx, Ny=nx // 2, Ma=Ma, shock_x=nx // 8,
+                        post=dict(rho=r2, T=T2 / sd["U2"], u=u2 / U)))
+    return dict(base="shock_drop_d2q9", instances=out)
+
+
 def main():
     out = dict(
         riemann_d2q9=riemann(),
@@ -102,6 +128,7 @@ def main():
         tgv_d3q27=tgv(),
         shock_drop_d3q27=_shock_drop(3, 1.47, 0.01),
     )
+    bt = batch()
     # parity cases: smaller noise amplitude reference sound speed per scenario
     for k, sc in out.items():
         if "vapour" in sc:
@@ -110,6 +137,7 @@ def main():
             sc["cs_ref"] = _cs_lattice(sc["right"]["rho"], sc["right"]["T"], sc["eos"])
         else:
             sc["cs_ref"] = sc["cs"]
+    out["batch_d2q9"] = bt
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "inputs", "scenarios.json")
     with open(path, "w") as fh:

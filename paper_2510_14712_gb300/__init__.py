@@ -32,7 +32,11 @@ EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
            "lbm_set_step_kernel", "lbm_autotune", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version",
-           "lbm_totals_noalloc", "lbm_totals_noalloc_error")
+           "lbm_totals_noalloc", "lbm_totals_noalloc_error",
+           "lbm_batch_create", "lbm_batch_set_boundary", "lbm_batch_set_stream", "lbm_batch_init",
+           "lbm_batch_step", "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_moments", "lbm_batch_flags",
+           "lbm_batch_autotune", "lbm_batch_nodes", "lbm_batch_launch_count", "lbm_batch_destroy",
+           "lbm_batch_last_error")
 
 
 class LbmError(RuntimeError):
@@ -85,6 +89,20 @@ def load():
         "lbm_version": (ctypes.c_char_p, []),
         "lbm_totals_noalloc": (I, [I, ctypes.c_longlong, P, P, P, D, D, P, P]),
         "lbm_totals_noalloc_error": (ctypes.c_char_p, []),
+        "lbm_batch_create": (I, [ctypes.POINTER(P), I, I, P, P, P, ctypes.POINTER(lbm_eos), D, D, D]),
+        "lbm_batch_set_boundary": (I, [P, I, I, I, dp]),
+        "lbm_batch_set_stream": (I, [P, P]),
+        "lbm_batch_init": (I, [P, I, P, P, P]),
+        "lbm_batch_step": (I, [P, I]),
+        "lbm_batch_step_async": (I, [P, I]),
+        "lbm_batch_sync": (I, [P]),
+        "lbm_batch_moments": (I, [P, I, P, P, P, P]),
+        "lbm_batch_flags": (I, [P, I, ctypes.POINTER(ctypes.c_uint)]),
+        "lbm_batch_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]),
+        "lbm_batch_nodes": (ctypes.c_longlong, [P]),
+        "lbm_batch_launch_count": (ctypes.c_longlong, [P]),
+        "lbm_batch_destroy": (I, [P]),
+        "lbm_batch_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +250,99 @@ def lbm_totals_noalloc(lattice, n, rho, u, T, a, cv, totals, stream_ptr=None):
 
 def lbm_version():
     return load().lbm_version().decode()
+
+
+# ---- batches ----------------------------------------------------------------------
+
+def _bcheck(rc):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_batch_last_error().decode())
+    return rc
+
+
+class Batch:
+    """Several ``inputs.Case`` instances (same lattice, fluid and precision) stepped together."""
+
+    def __init__(self, cases, precision="fp32"):
+        lib = load()
+        c0 = cases[0]
+        self.cases = list(cases)
+        self.D = c0.D
+        n = len(cases)
+        Nx = (ctypes.c_int * n)(*[c.shape[0] for c in cases])
+        Ny = (ctypes.c_int * n)(*[c.shape[1] for c in cases])
+        Nz = (ctypes.c_int * n)(*[(c.shape[2] if c.D == 3 else 1) for c in cases])
+        e = c0.eos
+        eos = lbm_eos(kind=0, a=e["a"], b=e["b"], R=e["R"], kappa=e["kappa"], eta_over_mu=e["eta_over_mu"],
+                      rho_ref=e["rho_ref"], T_ref=e["T_ref"], precision=PRECISIONS.get(precision, precision),
+                      closure=LBM_CLOSURE_EXACT)
+        self.b = ctypes.c_void_p()
+        _bcheck(lib.lbm_batch_create(ctypes.byref(self.b), c0.lattice, n, Nx, Ny, Nz, ctypes.byref(eos),
+                                     c0.tau, c0.Pr, c0.cv))
+        for k, c in enumerate(cases):
+            for face, spec in ((LBM_FACE_XLO, c.x_low), (LBM_FACE_XHI, c.x_high)):
+                if spec == "periodic":
+                    continue
+                if spec == "outflow":
+                    _bcheck(lib.lbm_batch_set_boundary(self.b, k, face, LBM_BC_OUTFLOW, None))
+                else:
+                    _, (rb, ub, Tb) = spec
+                    st = np.ascontiguousarray([rb] + list(ub)[:self.D] + [Tb], dtype=np.float64)
+                    _bcheck(lib.lbm_batch_set_boundary(self.b, k, face, LBM_BC_INFLOW,
+                                                       st.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def init(self):
+        lib = load()
+        for k, c in enumerate(self.cases):
+            rho = np.ascontiguousarray(c.rho, dtype=np.float64)
+            u = np.ascontiguousarray(np.stack(c.u), dtype=np.float64)
+            T = np.ascontiguousarray(c.T, dtype=np.float64)
+            _bcheck(lib.lbm_batch_init(self.b, k, _ptr(rho), _ptr(u), _ptr(T)))
+        return self
+
+    def step(self, n=1):
+        _bcheck(load().lbm_batch_step(self.b, n))
+        return self
+
+    def step_async(self, n=1):
+        _bcheck(load().lbm_batch_step_async(self.b, n))
+
+    def sync(self):
+        _bcheck(load().lbm_batch_sync(self.b))
+
+    def autotune(self, reps=3):
+        c, ms = ctypes.c_int(), ctypes.c_float()
+        _bcheck(load().lbm_batch_autotune(self.b, reps, ctypes.byref(c), ctypes.byref(ms)))
+        return c.value, ms.value
+
+    def fields(self, k):
+        c = self.cases[k]
+        shape = tuple(reversed(c.shape))
+        rho, u, T, tot = np.empty(shape), np.empty((c.D,) + shape), np.empty(shape), np.empty(c.D + 2)
+        _bcheck(load().lbm_batch_moments(self.b, k, _ptr(rho), _ptr(u), _ptr(T), _ptr(tot)))
+        return dict(rho=rho, u=u, T=T, totals=tot)
+
+    def flags(self, k):
+        f = ctypes.c_uint()
+        _bcheck(load().lbm_batch_flags(self.b, k, ctypes.byref(f)))
+        return f.value
+
+    def nodes(self):
+        return load().lbm_batch_nodes(self.b)
+
+    def launches(self):
+        return load().lbm_batch_launch_count(self.b)
+
+    def close(self):
+        if self.b:
+            load().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience wrapper -------------------------------------------------------

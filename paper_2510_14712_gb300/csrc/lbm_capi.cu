@@ -20,8 +20,6 @@ size_t scratch_bytes_d3_fp16(const Params&);
 
 using namespace lbm;
 
-// the opaque handle type of the C interface
-struct lbm_s : public Handle {};
 
 namespace {
 

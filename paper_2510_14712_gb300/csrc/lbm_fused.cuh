@@ -60,18 +60,18 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
   return v < 0 ? -v : (v >= T ? v - T + 1 : 0);
 }
 
-// MINB: CTAs per SM the register allocation must allow (2 keeps one CTA's
-// memory phase overlapping the other's collision).  SMALL: the box is
-// narrower than a tile plus its halo in x or y, so coordinates need an exact
-// modulo instead of a single conditional wrap.
-template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL>
-__global__ void __launch_bounds__(TX * TY, MINB)
-k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Store<S>::T* __restrict__ B,
-             unsigned* err, int ncolx, int ncoly, int nseg) {
+// One (column, z-segment) work item of the fused step: all planes mb..me-1 of
+// the TX x TY column at (x0, y0), reading A and writing B.  Shared by the
+// single-instance kernel and the batched persistent kernel.  SMALL: the box
+// is narrower than a tile plus its halo in x or y, so coordinates need an
+// exact modulo instead of a single conditional wrap.
+template <int D, typename S, typename real, int TX, int TY, bool SMALL>
+__device__ __forceinline__ void fused_column(const Params& p, const typename Store<S>::T* __restrict__ A,
+                                             typename Store<S>::T* __restrict__ B, int x0, int y0, int mb, int me,
+                                             unsigned char* smem_raw, unsigned& flags) {
   using L = Lattice<D>;
   using G = FusedGeom<D, TX, TY>;
   constexpr int Q = L::Q;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   real* s_rho = reinterpret_cast<real*>(smem_raw);            // [3][N3]
   real* s_mom = s_rho + 3 * G::N3;                            // [3][NMOM][N1]
   real* s_lap = s_mom + 3 * G::NMOM * G::N1;                  // [3][N2]
@@ -80,17 +80,233 @@ k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Stor
   const Model<real> m = model_of<real>(p);
   const int tid = threadIdx.x;
   const int Nm = D == 3 ? p.Nz : p.Ny;                        // march extent
-  const int Ny_in = D == 3 ? p.Ny : 1;                        // in-plane y extent
   const long long mstride = D == 3 ? (long long)p.Ny * p.pitch : (long long)p.pitch;
   const int xmin = p.periodic_x ? -0x40000000 : -3, xmax = p.periodic_x ? 0x40000000 : p.Nx + 2;
   using ST = typename Store<S>::T;
   // element offsets inside a population buffer fit 32 bits (checked at create)
   const unsigned plane32 = unsigned(p.plane), pitch32 = unsigned(p.pitch);
-  unsigned flags = 0;
 
-  // Work items are (column, z-segment) pairs, ordered segment-major so that
-  // the CTAs resident together cover neighbouring columns at the same planes
-  // and their halos are L2 hits.  nseg segments split the march axis.
+  for (int pl = mb - 3; pl <= me + 2; ++pl) {
+    // ---------------- A: moments of plane pl --------------------------------
+    // Direction-outer loop over this thread's positions of the R3 box: three
+    // per-plane base pointers and one 32-bit element offset per load
+    // (direction * plane + row + column).  j_a is accumulated as (sum over
+    // c_a = +1) minus (sum over c_a = -1), both in increasing direction order,
+    // so the two halves are computed identically for mirror-symmetric
+    // populations and j is then exactly zero (as the pairwise sum of Eq.
+    // def_u).  Positions 0 .. KFULL*NT-1 are spread over all threads; the
+    // remainder (fewer than NT) is done by the first threads only.
+    {
+      const int slot = (pl + 6) % 3;
+      const int mp = modp(pl, Nm);
+      const ST* Pm[3];
+#pragma unroll
+      for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
+      auto moments = [&](const int k) {
+        const int lx = k % G::BX3, ly = k / G::BX3;
+        const int ox = outside(lx, 3, TX), oy = D == 3 ? outside(ly, G::HY3, TY) : 0;
+        const int gx = x0 + lx - 3;
+        if (ox + oy > 3 || gx < xmin || gx > xmax) return;
+        const bool in1 = ox + oy <= 1;
+        const int gy = D == 3 ? wrapc<SMALL>(y0 + ly - G::HY3, p.Ny) : 0;
+        unsigned xc[3], yr[3];
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) {
+          xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
+          yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
+        }
+        real rho = real(0), sp[D], sn[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) sp[a] = sn[a] = real(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
+          const real v = Store<S>::template ld<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
+                                                     p.ref[i]);
+          rho += v;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            if (L::c(i, a) == 1) sp[a] += v;
+            if (L::c(i, a) == -1) sn[a] += v;
+          }
+        }
+        s_rho[slot * G::N3 + k] = rho;
+        if (in1) {
+          real Se = real(0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
+            Se += Store<S>::template ld<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
+                                              p.ref[Q + i]);
+          }
+          const int k1 = (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx - 2);
+          real* dst = s_mom + (slot * G::NMOM) * G::N1 + k1;
+#pragma unroll
+          for (int a = 0; a < D; ++a) dst[a * G::N1] = sp[a] - sn[a];
+          dst[D * G::N1] = Se;
+        }
+      };
+      constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
+#pragma unroll 1
+      for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
+      if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
+    }
+    __syncthreads();
+
+    // ---------------- B: Laplacian of rho, plane pl-1, on R2 ------------------
+    if (pl - 1 >= mb - 2) {
+      const int q = pl - 1;
+      const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
+      for (int k = tid; k < G::N2; k += G::NT) {
+        const int lx = k % G::BX2, ly = k / G::BX2;
+        const int ox = outside(lx, 2, TX), oy = D == 3 ? outside(ly, G::HY2, TY) : 0;
+        if (ox + oy > 2) continue;
+        const int gx = x0 + lx - 2;
+        if (gx < xmin + 1 || gx > xmax - 1) continue;
+        const int k3 = (ly + (G::HY3 - G::HY2)) * G::BX3 + (lx + 1);
+        const real* r = s_rho + sc * G::N3;
+        const real c2 = real(2) * r[k3];
+        real lap = (r[k3 + 1] + r[k3 - 1] - c2) + (s_rho[sp * G::N3 + k3] + s_rho[sm * G::N3 + k3] - c2);
+        if (D == 3) lap += r[k3 + G::BX3] + r[k3 - G::BX3] - c2;
+        s_lap[sc * G::N2 + k] = lap;
+      }
+    }
+    __syncthreads();
+
+    // ---------------- C: primitive fields, plane pl-2, on R1 ------------------
+    if (pl - 2 >= mb - 1) {
+      const int q = pl - 2;
+      const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
+      for (int k = tid; k < G::N1; k += G::NT) {
+        const int lx = k % G::BX1, ly = k / G::BX1;
+        const int ox = outside(lx, 1, TX), oy = D == 3 ? outside(ly, G::HY1, TY) : 0;
+        if (ox + oy > 1) continue;
+        const int gx = x0 + lx - 1;
+        if (gx < xmin + 2 || gx > xmax - 2) continue;
+        const int k3 = (ly + (G::HY3 - G::HY1)) * G::BX3 + (lx + 2);
+        const int k2 = (ly + (G::HY2 - G::HY1)) * G::BX2 + (lx + 1);
+        const real rho = s_rho[sc * G::N3 + k3];
+        const real* lp = s_lap + sc * G::N2;
+        real F[D];
+        F[0] = m.kappa * rho * real(0.5) * (lp[k2 + 1] - lp[k2 - 1]);                         // Eq. FK
+        if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
+        F[D - 1] = m.kappa * rho * real(0.5) * (s_lap[sp * G::N2 + k2] - s_lap[sm * G::N2 + k2]);
+        const real* mo = s_mom + (sc * G::NMOM) * G::N1 + k;
+        real u[D], uF = 0, u2 = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          u[a] = (mo[a * G::N1] + real(0.5) * F[a]) / rho;                                     // Eq. def_u
+          uF += u[a] * F[a];
+          u2 += u[a] * u[a];
+        }
+        const real E = (mo[D * G::N1] + real(0.5) * uF) / rho;                                // Eq. def_E
+        const real T = (E - real(0.5) * u2 + m.a * rho) / m.cv;                                 // Eq. lbm_temp
+        const real P = vdw_pressure(m, rho, T);
+        const real theta = P / rho;
+        real* pr = s_prm + (sc * G::NPRIM) * G::N1 + k;
+        pr[G::P_RHO * G::N1] = rho;
+        pr[G::P_T * G::N1] = T;
+        pr[G::P_H * G::N1] = vdw_energy(m, rho, T) + theta;                                   // Eq. enthalpy
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          pr[(G::P_U + a) * G::N1] = u[a];
+          pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
+          pr[(G::P_F + a) * G::N1] = F[a];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- D: collide plane pl-3 on the tile --------------------------
+    if (pl - 3 >= mb) {
+      const int q = pl - 3;
+      const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
+      const int lx = tid % TX, ly = tid / TX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx < p.Nx && (D == 2 || gy < p.Ny)) {
+        const int mq = modp(q, Nm);
+        const ST* Pm[3];
+        unsigned xc[3], yr[3];
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) {
+          Pm[c + 1] = A + (long long)wrap(mq - c, Nm) * mstride;
+          xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
+          yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
+        }
+        ST* Bq = B + (long long)mq * mstride;
+        const int k1 = (ly + G::HY1) * G::BX1 + (lx + 1);
+        const real* pc = s_prm + (sc * G::NPRIM) * G::N1;
+        const real* pm = s_prm + (sm * G::NPRIM) * G::N1;
+        const real* pp = s_prm + (sp * G::NPRIM) * G::N1;
+        NodeState<D, real> s;
+        s.rho = pc[G::P_RHO * G::N1 + k1];
+        s.T = pc[G::P_T * G::N1 + k1];
+        s.div_u = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          s.u[a] = pc[(G::P_U + a) * G::N1 + k1];
+          s.F[a] = pc[(G::P_F + a) * G::N1 + k1];
+        }
+        // neighbour accessors along axis a: (plane pointer, index) of -1 / +1
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const real *bm, *bp;
+          int km, kp;
+          if (a == D - 1) { bm = pm; bp = pp; km = kp = k1; }
+          else if (a == 0) { bm = bp = pc; km = k1 - 1; kp = k1 + 1; }
+          else { bm = bp = pc; km = k1 - G::BX1; kp = k1 + G::BX1; }
+          s.div_u += real(0.5) * (bp[(G::P_U + a) * G::N1 + kp] - bm[(G::P_U + a) * G::N1 + km]);
+          s.gradT[a] = real(0.5) * (bp[G::P_T * G::N1 + kp] - bm[G::P_T * G::N1 + km]);
+          s.gradh[a] = real(0.5) * (bp[G::P_H * G::N1 + kp] - bm[G::P_H * G::N1 + km]);
+          const real lc = pc[(G::P_LAM + a) * G::N1 + k1];
+          const real back = lc - bm[(G::P_LAM + a) * G::N1 + km];
+          const real fwd = bp[(G::P_LAM + a) * G::N1 + kp] - lc;
+          s.dLam[a] = s.u[a] > real(0) ? back : (s.u[a] < real(0) ? fwd : real(0.5) * (back + fwd));
+        }
+        Attractors<D, real> at;
+        at.setup(m, s);
+        flags |= at.flags;
+        const unsigned oc = yr[1] + xc[1];                  // own in-plane offset
+        // f pass then g pass: one population set in flight at a time
+        real v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
+          v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
+                                                 p.ref[i]);
+        }
+        FactoredRelax<D, real>::f_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
+          Store<S>::template st_stream<real>(Bq, unsigned(i) * plane32 + oc, x, p.ref[i]);
+        });
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
+          v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
+                                                 p.ref[Q + i]);
+        }
+        FactoredRelax<D, real>::g_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
+          Store<S>::template st_stream<real>(Bq, unsigned(Q + i) * plane32 + oc, x, p.ref[Q + i]);
+        });
+      }
+    }
+    // no barrier needed here: the next write to the primitive ring (stage C)
+    // comes after the two barriers of stages A and B of the next plane
+  }
+  __syncthreads();   // rings are reused by the next work item
+}
+
+// Single-instance step: work items are (column, z-segment) pairs, ordered
+// segment-major so that the CTAs resident together cover neighbouring
+// columns at the same planes and their halos are L2 hits.  MINB: CTAs per SM
+// the register allocation must allow (2 keeps one CTA's memory phase
+// overlapping the other's collision).
+template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL>
+__global__ void __launch_bounds__(TX * TY, MINB)
+k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __restrict__ A,
+             typename Store<S>::T* __restrict__ B, unsigned* err, int ncolx, int ncoly, int nseg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned flags = 0;
+  const int Nm = D == 3 ? p.Nz : p.Ny;
   const int ncol = ncolx * ncoly;
   const long long nitems = (long long)ncol * nseg;
   for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -99,216 +315,84 @@ k_step_fused(Params p, const typename Store<S>::T* __restrict__ A, typename Stor
     const int mb = int((long long)Nm * seg / nseg), me = int((long long)Nm * (seg + 1) / nseg);
     const int x0 = (col % ncolx) * TX;
     const int y0 = D == 3 ? (col / ncolx) * TY : 0;
-
-    for (int pl = mb - 3; pl <= me + 2; ++pl) {
-      // ---------------- A: moments of plane pl --------------------------------
-      // Direction-outer loop over this thread's positions of the R3 box: three
-      // per-plane base pointers and one 32-bit element offset per load
-      // (direction * plane + row + column).  j_a is accumulated as (sum over
-      // c_a = +1) minus (sum over c_a = -1), both in increasing direction order,
-      // so the two halves are computed identically for mirror-symmetric
-      // populations and j is then exactly zero (as the pairwise sum of Eq.
-      // def_u).  Positions 0 .. KFULL*NT-1 are spread over all threads; the
-      // remainder (fewer than NT) is done by the first threads only.
-      {
-        const int slot = (pl + 6) % 3;
-        const int mp = modp(pl, Nm);
-        const ST* Pm[3];
-#pragma unroll
-        for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
-        auto moments = [&](const int k) {
-          const int lx = k % G::BX3, ly = k / G::BX3;
-          const int ox = outside(lx, 3, TX), oy = D == 3 ? outside(ly, G::HY3, TY) : 0;
-          const int gx = x0 + lx - 3;
-          if (ox + oy > 3 || gx < xmin || gx > xmax) return;
-          const bool in1 = ox + oy <= 1;
-          const int gy = D == 3 ? wrapc<SMALL>(y0 + ly - G::HY3, p.Ny) : 0;
-          unsigned xc[3], yr[3];
-#pragma unroll
-          for (int c = -1; c <= 1; ++c) {
-            xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
-            yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
-          }
-          real rho = real(0), sp[D], sn[D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) sp[a] = sn[a] = real(0);
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            const real v = Store<S>::template ld<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                       p.ref[i]);
-            rho += v;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-              if (L::c(i, a) == 1) sp[a] += v;
-              if (L::c(i, a) == -1) sn[a] += v;
-            }
-          }
-          s_rho[slot * G::N3 + k] = rho;
-          if (in1) {
-            real Se = real(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-              const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-              Se += Store<S>::template ld<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                p.ref[Q + i]);
-            }
-            const int k1 = (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx - 2);
-            real* dst = s_mom + (slot * G::NMOM) * G::N1 + k1;
-#pragma unroll
-            for (int a = 0; a < D; ++a) dst[a * G::N1] = sp[a] - sn[a];
-            dst[D * G::N1] = Se;
-          }
-        };
-        constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
-#pragma unroll 1
-        for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
-        if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
-      }
-      __syncthreads();
-
-      // ---------------- B: Laplacian of rho, plane pl-1, on R2 ------------------
-      if (pl - 1 >= mb - 2) {
-        const int q = pl - 1;
-        const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
-        for (int k = tid; k < G::N2; k += G::NT) {
-          const int lx = k % G::BX2, ly = k / G::BX2;
-          const int ox = outside(lx, 2, TX), oy = D == 3 ? outside(ly, G::HY2, TY) : 0;
-          if (ox + oy > 2) continue;
-          const int gx = x0 + lx - 2;
-          if (gx < xmin + 1 || gx > xmax - 1) continue;
-          const int k3 = (ly + (G::HY3 - G::HY2)) * G::BX3 + (lx + 1);
-          const real* r = s_rho + sc * G::N3;
-          const real c2 = real(2) * r[k3];
-          real lap = (r[k3 + 1] + r[k3 - 1] - c2) + (s_rho[sp * G::N3 + k3] + s_rho[sm * G::N3 + k3] - c2);
-          if (D == 3) lap += r[k3 + G::BX3] + r[k3 - G::BX3] - c2;
-          s_lap[sc * G::N2 + k] = lap;
-        }
-      }
-      __syncthreads();
-
-      // ---------------- C: primitive fields, plane pl-2, on R1 ------------------
-      if (pl - 2 >= mb - 1) {
-        const int q = pl - 2;
-        const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
-        for (int k = tid; k < G::N1; k += G::NT) {
-          const int lx = k % G::BX1, ly = k / G::BX1;
-          const int ox = outside(lx, 1, TX), oy = D == 3 ? outside(ly, G::HY1, TY) : 0;
-          if (ox + oy > 1) continue;
-          const int gx = x0 + lx - 1;
-          if (gx < xmin + 2 || gx > xmax - 2) continue;
-          const int k3 = (ly + (G::HY3 - G::HY1)) * G::BX3 + (lx + 2);
-          const int k2 = (ly + (G::HY2 - G::HY1)) * G::BX2 + (lx + 1);
-          const real rho = s_rho[sc * G::N3 + k3];
-          const real* lp = s_lap + sc * G::N2;
-          real F[D];
-          F[0] = m.kappa * rho * real(0.5) * (lp[k2 + 1] - lp[k2 - 1]);                         // Eq. FK
-          if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
-          F[D - 1] = m.kappa * rho * real(0.5) * (s_lap[sp * G::N2 + k2] - s_lap[sm * G::N2 + k2]);
-          const real* mo = s_mom + (sc * G::NMOM) * G::N1 + k;
-          real u[D], uF = 0, u2 = 0;
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            u[a] = (mo[a * G::N1] + real(0.5) * F[a]) / rho;                                     // Eq. def_u
-            uF += u[a] * F[a];
-            u2 += u[a] * u[a];
-          }
-          const real E = (mo[D * G::N1] + real(0.5) * uF) / rho;                                // Eq. def_E
-          const real T = (E - real(0.5) * u2 + m.a * rho) / m.cv;                                 // Eq. lbm_temp
-          const real P = vdw_pressure(m, rho, T);
-          const real theta = P / rho;
-          real* pr = s_prm + (sc * G::NPRIM) * G::N1 + k;
-          pr[G::P_RHO * G::N1] = rho;
-          pr[G::P_T * G::N1] = T;
-          pr[G::P_H * G::N1] = vdw_energy(m, rho, T) + theta;                                   // Eq. enthalpy
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            pr[(G::P_U + a) * G::N1] = u[a];
-            pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
-            pr[(G::P_F + a) * G::N1] = F[a];
-          }
-        }
-      }
-      __syncthreads();
-
-      // ---------------- D: collide plane pl-3 on the tile --------------------------
-      if (pl - 3 >= mb) {
-        const int q = pl - 3;
-        const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
-        const int lx = tid % TX, ly = tid / TX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx < p.Nx && (D == 2 || gy < p.Ny)) {
-          const int mq = modp(q, Nm);
-          const ST* Pm[3];
-          unsigned xc[3], yr[3];
-#pragma unroll
-          for (int c = -1; c <= 1; ++c) {
-            Pm[c + 1] = A + (long long)wrap(mq - c, Nm) * mstride;
-            xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
-            yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
-          }
-          ST* Bq = B + (long long)mq * mstride;
-          const int k1 = (ly + G::HY1) * G::BX1 + (lx + 1);
-          const real* pc = s_prm + (sc * G::NPRIM) * G::N1;
-          const real* pm = s_prm + (sm * G::NPRIM) * G::N1;
-          const real* pp = s_prm + (sp * G::NPRIM) * G::N1;
-          NodeState<D, real> s;
-          s.rho = pc[G::P_RHO * G::N1 + k1];
-          s.T = pc[G::P_T * G::N1 + k1];
-          s.div_u = 0;
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            s.u[a] = pc[(G::P_U + a) * G::N1 + k1];
-            s.F[a] = pc[(G::P_F + a) * G::N1 + k1];
-          }
-          // neighbour accessors along axis a: (plane pointer, index) of -1 / +1
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            const real *bm, *bp;
-            int km, kp;
-            if (a == D - 1) { bm = pm; bp = pp; km = kp = k1; }
-            else if (a == 0) { bm = bp = pc; km = k1 - 1; kp = k1 + 1; }
-            else { bm = bp = pc; km = k1 - G::BX1; kp = k1 + G::BX1; }
-            s.div_u += real(0.5) * (bp[(G::P_U + a) * G::N1 + kp] - bm[(G::P_U + a) * G::N1 + km]);
-            s.gradT[a] = real(0.5) * (bp[G::P_T * G::N1 + kp] - bm[G::P_T * G::N1 + km]);
-            s.gradh[a] = real(0.5) * (bp[G::P_H * G::N1 + kp] - bm[G::P_H * G::N1 + km]);
-            const real lc = pc[(G::P_LAM + a) * G::N1 + k1];
-            const real back = lc - bm[(G::P_LAM + a) * G::N1 + km];
-            const real fwd = bp[(G::P_LAM + a) * G::N1 + kp] - lc;
-            s.dLam[a] = s.u[a] > real(0) ? back : (s.u[a] < real(0) ? fwd : real(0.5) * (back + fwd));
-          }
-          Attractors<D, real> at;
-          at.setup(m, s);
-          flags |= at.flags;
-          const unsigned oc = yr[1] + xc[1];                  // own in-plane offset
-          // f pass then g pass: one population set in flight at a time
-          real v[Q];
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                   p.ref[i]);
-          }
-          FactoredRelax<D, real>::f_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
-            Store<S>::template st_stream<real>(Bq, unsigned(i) * plane32 + oc, x, p.ref[i]);
-          });
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                   p.ref[Q + i]);
-          }
-          FactoredRelax<D, real>::g_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
-            Store<S>::template st_stream<real>(Bq, unsigned(Q + i) * plane32 + oc, x, p.ref[Q + i]);
-          });
-        }
-      }
-      // no barrier needed here: the next write to the primitive ring (stage C)
-      // comes after the two barriers of stages A and B of the next plane
-    }
-    __syncthreads();   // rings are reused by the next segment
+    fused_column<D, S, real, TX, TY, SMALL>(p, A, B, x0, y0, mb, me, smem_raw, flags);
   }
   if (flags) atomicOr(err, flags);
+}
+
+// One instance of a batch: its parameters, its two population buffers and its
+// column count along x (ncoly = 1 in 2-D; 3-D columns are ncolx per y-row).
+struct BatchInstance {
+  Params p;
+  void* pop[2];
+  int ncolx, ncoly;
+  int pad[2];
+};
+
+// One work item of a batch step: instance, column, plane range.
+struct BatchItem {
+  int inst, col, mb, me;
+};
+
+// Batched step: one persistent launch over the work items of every instance
+// (sorted longest first), taken dynamically from an atomic counter so that
+// uneven instances balance.  `parity` selects which buffer of each instance is
+// the source.  Fatal / warning bits go to the instance's word in `errs`.
+// SMALL instances are handled by the exact-modulo variant of the column body.
+template <int D, typename S, typename real, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+k_step_fused_batch(const BatchInstance* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
+                   int parity, int* counter, unsigned* errs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  using ST = typename Store<S>::T;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem w = items[it];
+    const BatchInstance& bi = insts[w.inst];
+    const Params& p = bi.p;
+    const ST* A = reinterpret_cast<const ST*>(bi.pop[parity]);
+    ST* B = reinterpret_cast<ST*>(bi.pop[parity ^ 1]);
+    const int x0 = (w.col % bi.ncolx) * TX;
+    const int y0 = D == 3 ? (w.col / bi.ncolx) * TY : 0;
+    unsigned flags = 0;
+    const bool small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
+    if (small) fused_column<D, S, real, TX, TY, true>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags);
+    else fused_column<D, S, real, TX, TY, false>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags);
+    if (flags) atomicOr(errs + w.inst, flags);
+  }
+}
+
+// Batched ghost fill: block b refills the x ghost layers of instance b (if its
+// x faces are not periodic), as k_ghosts does for one instance.
+template <int D, typename S>
+__global__ void k_ghosts_batch(const BatchInstance* __restrict__ insts, int parity) {
+  using L = Lattice<D>;
+  using ST = typename Store<S>::T;
+  const BatchInstance& bi = insts[blockIdx.x];
+  const Params& p = bi.p;
+  if (p.periodic_x) return;
+  ST* Bp = reinterpret_cast<ST*>(bi.pop[parity ^ 1]);
+  const long long n = 2LL * p.G * p.Ny * p.Nz;
+  for (long long gid = threadIdx.x; gid < n; gid += blockDim.x) {
+    const int g = int(gid % (2 * p.G));
+    const long long r = gid / (2 * p.G);
+    const int y = int(r % p.Ny), z = int(r / p.Ny);
+    const bool low = g < p.G;
+    const int xp = low ? g : p.Nx + g;
+    const int bc = low ? p.bc_lo : p.bc_hi;
+    const long long o = ((long long)z * p.Ny + y) * p.pitch + xp;
+    const long long os = ((long long)z * p.Ny + y) * p.pitch + (low ? p.G : p.G + p.Nx - 1);
+    const double* eq = low ? p.eq_lo : p.eq_hi;
+    for (int i = 0; i < 2 * L::Q; ++i) {
+      if (bc == LBM_BC_INFLOW) Store<S>::template st<double>(Bp, i * p.plane + o, eq[i], p.ref[i]);
+      else Bp[i * p.plane + o] = Bp[i * p.plane + os];
+    }
+  }
 }
 
 }  // namespace lbm

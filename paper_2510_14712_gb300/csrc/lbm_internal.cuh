@@ -65,6 +65,8 @@ struct Handle {
   long long launches;
 };
 
+struct Batch;
+
 // Per (D, precision) kernel set.
 struct Ops {
   // state[i] at every padded node from FP64 device fields (interior layout)
@@ -77,7 +79,39 @@ struct Ops {
   void (*macro)(Handle& h, const void* src, double* rho, double* u, double* T, double* totals);
   // time the fused kernel's tile shapes, keep the fastest; returns its index
   int (*autotune)(Handle& h, int reps, float* best_ms);
+  // batches: number of tile shapes; build the device instance table and the
+  // sorted work list of shape cfg; enqueue one batched step from `parity`
+  int (*batch_ncfg)();
+  int (*batch_prepare)(Batch& b, int cfg);
+  void (*batch_enqueue)(Batch& b, int parity);
 };
+
+// A batch of instances stepped together (lbm_batch_* in include/lbm.h).
+struct Batch {
+  int n, D, Q, precision;
+  Handle** inst;              // one handle per instance (own buffers and scratch)
+  void* d_insts;              // device table of BatchInstance
+  void* d_items;              // device work list of BatchItem, longest first
+  int nitems;
+  int* d_counter;             // work-list counter of the persistent kernel
+  unsigned* d_errs;           // status word per instance
+  unsigned* h_errs;           // pinned copy
+  cudaStream_t stream;
+  int own_stream;
+  int cur;                    // parity of the current state (same for all instances)
+  int tile_cfg;
+  int grid;                   // persistent CTAs
+  cudaGraphExec_t graph[2];   // one step from parity 0 / 1
+  int graph_ready;
+  int unstable;
+  long long launches;
+};
+
+// the opaque handle type of the C interface
+}  // namespace lbm
+struct lbm_s : public lbm::Handle {};
+struct lbm_batch_s : public lbm::Batch {};
+namespace lbm {
 
 const Ops* ops_d2_fp64();
 const Ops* ops_d2_fp32();

@@ -2,6 +2,9 @@
 // Each k_*.cu translation unit instantiates one of them.
 #pragma once
 
+#include <algorithm>
+#include <vector>
+
 #include "lbm_fused.cuh"
 
 namespace lbm {
@@ -183,8 +186,100 @@ template <int D, typename S, typename real> struct OpsImpl {
 
   static size_t scratch_bytes(const Params& p) { return size_t(4 * D + 4) * size_t(p.plane) * sizeof(real); }
 
+  // ---- batches -------------------------------------------------------------
+  template <int TX, int TY, int MINB> struct BatchFused {
+    using FG = FusedGeom<D, TX, TY>;
+    static int prepare(Batch& b) {
+      std::vector<BatchInstance> ti(b.n);
+      std::vector<BatchItem> items;
+      const int seg_len = 128;                                // planes per work item (long columns split)
+      for (int k = 0; k < b.n; ++k) {
+        const Handle& h = *b.inst[k];
+        BatchInstance& bi = ti[k];
+        bi.p = h.p;
+        bi.pop[0] = h.pop[0];
+        bi.pop[1] = h.pop[1];
+        bi.ncolx = (h.p.Nx + TX - 1) / TX;
+        bi.ncoly = D == 3 ? (h.p.Ny + TY - 1) / TY : 1;
+        const int Nm = D == 3 ? h.p.Nz : h.p.Ny;
+        const int nseg = Nm > seg_len ? (Nm + seg_len - 1) / seg_len : 1;
+        for (int c = 0; c < bi.ncolx * bi.ncoly; ++c)
+          for (int sg = 0; sg < nseg; ++sg)
+            items.push_back({k, c, int((long long)Nm * sg / nseg), int((long long)Nm * (sg + 1) / nseg)});
+      }
+      std::stable_sort(items.begin(), items.end(),
+                       [](const BatchItem& a, const BatchItem& c) { return a.me - a.mb > c.me - c.mb; });
+      if (b.d_insts) cudaFree(b.d_insts);
+      if (b.d_items) cudaFree(b.d_items);
+      b.d_insts = b.d_items = nullptr;
+      if (cudaMalloc(&b.d_insts, sizeof(BatchInstance) * b.n) != cudaSuccess) return LBM_ENOMEM;
+      if (cudaMalloc(&b.d_items, sizeof(BatchItem) * items.size()) != cudaSuccess) return LBM_ENOMEM;
+      cudaMemcpy(b.d_insts, ti.data(), sizeof(BatchInstance) * b.n, cudaMemcpyHostToDevice);
+      cudaMemcpy(b.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+      b.nitems = int(items.size());
+      const size_t smem = FG::template smem_bytes<real>();
+      auto kern = k_step_fused_batch<D, S, real, TX, TY, MINB>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      int bps = 1, sms = 1, dev = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, FG::NT, smem);
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      b.grid = (bps < 1 ? 1 : bps) * sms;
+      if (b.grid > b.nitems) b.grid = b.nitems;
+      return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    }
+    static void enqueue(Batch& b, int parity) {
+      cudaMemsetAsync(b.d_counter, 0, sizeof(int), b.stream);
+      k_step_fused_batch<D, S, real, TX, TY, MINB><<<b.grid, FG::NT, FG::template smem_bytes<real>(), b.stream>>>(
+          reinterpret_cast<const BatchInstance*>(b.d_insts), reinterpret_cast<const BatchItem*>(b.d_items), b.nitems,
+          parity, b.d_counter, b.d_errs);
+      k_ghosts_batch<D, S><<<b.n, 256, 0, b.stream>>>(reinterpret_cast<const BatchInstance*>(b.d_insts), parity);
+      b.launches += 2;
+    }
+  };
+
+  using PrepFn = int (*)(Batch&);
+  using EnqFn = void (*)(Batch&, int);
+  static int batch_cands(const PrepFn** pf, const EnqFn** ef) {
+    if (D == 3) {
+      if (sizeof(real) == 8) {
+        static const PrepFn p[] = {&BatchFused<32, 8, 1>::prepare};
+        static const EnqFn e[] = {&BatchFused<32, 8, 1>::enqueue};
+        *pf = p; *ef = e;
+        return 1;
+      }
+      static const PrepFn p[] = {&BatchFused<32, 8, 2>::prepare, &BatchFused<16, 16, 2>::prepare};
+      static const EnqFn e[] = {&BatchFused<32, 8, 2>::enqueue, &BatchFused<16, 16, 2>::enqueue};
+      *pf = p; *ef = e;
+      return 2;
+    }
+    static const PrepFn p[] = {&BatchFused<256, 1, 2>::prepare, &BatchFused<128, 1, 4>::prepare,
+                               &BatchFused<64, 1, 8>::prepare};
+    static const EnqFn e[] = {&BatchFused<256, 1, 2>::enqueue, &BatchFused<128, 1, 4>::enqueue,
+                              &BatchFused<64, 1, 8>::enqueue};
+    *pf = p; *ef = e;
+    return 3;
+  }
+  static int batch_ncfg() {
+    const PrepFn* pf;
+    const EnqFn* ef;
+    return batch_cands(&pf, &ef);
+  }
+  static int batch_prepare(Batch& b, int cfg) {
+    const PrepFn* pf;
+    const EnqFn* ef;
+    const int n = batch_cands(&pf, &ef);
+    return pf[cfg < n ? cfg : 0](b);
+  }
+  static void batch_enqueue(Batch& b, int parity) {
+    const PrepFn* pf;
+    const EnqFn* ef;
+    const int n = batch_cands(&pf, &ef);
+    ef[b.tile_cfg < n ? b.tile_cfg : 0](b, parity);
+  }
+
   static const Ops* ops() {
-    static const Ops o = {&init, &step, &step_multipass, &macro, &autotune};
+    static const Ops o = {&init, &step, &step_multipass, &macro, &autotune, &batch_ncfg, &batch_prepare, &batch_enqueue};
     return &o;
   }
 };
