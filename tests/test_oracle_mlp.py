@@ -1,0 +1,112 @@
+"""Pins of the FP64 MLP oracle of the learned closure (oracle/mlp.py)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import norm
+
+import inputs
+from oracle import mlp, thermo
+
+
+def params(seed=3):
+    return mlp.init_params(inputs.uniform(seed, mlp.NPARAM))
+
+
+def data(n=37, seed=9):
+    X = np.stack([inputs.uniform(seed, n), inputs.uniform(seed + 1, n)], axis=1)
+    Y = np.stack([np.sin(X[:, 0]) * X[:, 1], X[:, 0] ** 2 - 0.3, np.cos(X[:, 1])], axis=1)
+    return X, Y
+
+
+def test_backward_matches_central_differences():
+    theta = params()
+    X, Y = data()
+    _, g = mlp.loss_and_grad(theta, X, Y)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(mlp.NPARAM, 60, replace=False)
+    h = 1e-6
+    for k in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (mlp.loss_and_grad(tp, X, Y)[0] - mlp.loss_and_grad(tm, X, Y)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1e-3, abs(g[k])) + 1e-11, (k, fd, g[k])
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    v = np.concatenate([inputs.uniform(5, 1000) * 10.0 ** np.arange(-5, 5).repeat(100),
+                        [1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 0.0]]).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.to_bf16(v), ref)
+    assert mlp.to_bf16(np.float32(1.0 + 2 ** -8)) == 1.0            # tie to even
+    assert mlp.to_bf16(np.float32(1.0 + 3 * 2 ** -8)) == 1.0 + 2 ** -6
+
+
+def test_gelu_tanh_form_approximates_x_times_normal_cdf():
+    """The tanh form stays within 5e-4 of z Phi(z) (Hendrycks & Gimpel) and is odd up to z."""
+    z = np.linspace(-8, 8, 1601)
+    err = np.abs(mlp.gelu(z) - z * norm.cdf(z))
+    assert err.max() < 5e-4
+    assert err.max() > 1e-5                      # it is the approximation, not the erf form
+    assert np.allclose(mlp.gelu(z) - mlp.gelu(-z), z, atol=1e-14)
+    assert mlp.gelu(0.0) == 0.0
+    h = 1e-6
+    assert np.allclose(mlp.gelu_grad(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h), atol=1e-8)
+
+
+def test_quantize_rounds_weights_not_biases():
+    th = params() + 1e-3 * inputs.uniform(11, mlp.NPARAM)
+    q = mlp.unpack(mlp.quantize(th))
+    p = mlp.unpack(th)
+    for name, _ in mlp.SHAPES:
+        if name.startswith("W"):
+            assert np.array_equal(q[name], mlp.to_bf16(p[name]))
+        else:
+            assert np.array_equal(q[name], np.float32(p[name]).astype(np.float64))
+
+
+def test_closure_gate_uses_exact_relations_outside_the_box():
+    a, b, R, cv = 0.25, 1 / 3, 8 / 3, 8.0
+    theta = params()
+    scale = np.array([0.6, 0.3, 0.5, 0.2, 0.1, 0.05, 0.2, 0.1, 0.3, 0.1])
+    rho = np.array([0.5, 0.95, 0.2, 0.61])
+    e = np.array([0.45, 0.5, 0.5, 0.75])
+    T, P, c2, used = mlp.closure(theta, scale, rho, e, a, b, R, cv)
+    assert used.tolist() == [True, False, False, False]
+    Te, Pe, ce = mlp.vdw_targets(rho, e, a, b, R, cv)
+    assert np.array_equal(T[1:], Te[1:]) and np.array_equal(P[1:], Pe[1:]) and np.array_equal(c2[1:], ce[1:])
+    y, _ = mlp.forward(theta, np.array([[(0.5 - 0.6) / 0.3, (0.45 - 0.5) / 0.2]]))
+    assert np.allclose([T[0], P[0], c2[0]], [0.1 + 0.05 * y[0, 0], 0.2 + 0.1 * y[0, 1], 0.3 + 0.1 * y[0, 2]],
+                       rtol=1e-15)
+
+
+def test_adamw_first_step_is_signed_lr():
+    """With m = v = 0 the bias-corrected first step is lr * g/(|g| + eps) (Kingma & Ba)."""
+    g = np.array([0.3, -2.0, 1e-3])
+    th, m, v = mlp.adamw_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    assert np.allclose(th, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    th, _, _ = mlp.adamw_step(np.ones(3), np.zeros(3), np.zeros(3), np.zeros(3), 1, lr=0.1, wd=0.5)
+    assert np.allclose(th, 1.0 - 0.1 * 0.5)
+
+
+def test_targets_are_the_oracle_closure():
+    rho = np.array([0.3, 0.6, 0.9]); T = np.array([0.09, 0.15, 0.12])
+    a, b, R, cv = 0.25, 1 / 3, 8 / 3, 8.0
+    e = thermo.internal_energy(rho, T, a, cv)
+    Tt, P, cs2 = mlp.vdw_targets(rho, e, a, b, R, cv)
+    assert np.allclose(Tt, T, rtol=1e-15)
+    assert np.allclose(P, thermo.pressure(rho, T, a, b, R), rtol=1e-15)
+    assert np.allclose(cs2, thermo.sound_speed_sq(rho, T, a, b, R, cv), rtol=1e-15)
+
+
+def test_training_reduces_loss():
+    theta = params()
+    X, Y = data(200)
+    m = np.zeros_like(theta); v = np.zeros_like(theta)
+    l0 = mlp.loss_and_grad(theta, X, Y)[0]
+    for t in range(1, 301):
+        _, g = mlp.loss_and_grad(theta, X, Y)
+        theta, m, v = mlp.adamw_step(theta, g, m, v, t, lr=3e-3)
+    assert mlp.loss_and_grad(theta, X, Y)[0] < 0.05 * l0
