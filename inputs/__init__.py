@@ -25,10 +25,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 
 
-def splitmix64(seed, n):
-    """n outputs of SplitMix64 started at state ``seed`` (uint64 array)."""
+def splitmix64(seed, n, start=0):
+    """Outputs start .. start + n - 1 of SplitMix64 started at state ``seed`` (uint64 array)."""
     with np.errstate(over="ignore"):
-        k = np.arange(1, n + 1, dtype=np.uint64)
+        k = np.arange(start + 1, start + n + 1, dtype=np.uint64)
         z = np.uint64(seed) + k * _GAMMA
         z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
         z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
@@ -36,9 +36,9 @@ def splitmix64(seed, n):
     return z
 
 
-def uniform(seed, n):
-    """n values uniform in [-1, 1) from ``splitmix64(seed, n)``."""
-    z = splitmix64(seed, n) >> np.uint64(11)
+def uniform(seed, n, start=0):
+    """n values uniform in [-1, 1) from ``splitmix64(seed, n, start)``."""
+    z = splitmix64(seed, n, start) >> np.uint64(11)
     return z.astype(np.float64) * (2.0 ** -52) - 1.0
 
 
@@ -195,3 +195,48 @@ def add_noise(c, seed, rel=1e-3):
     c.rho = c.rho * (1.0 + rel * uniform(seed, n).reshape(c.rho.shape))
     c.u = [ua + rel * cs * uniform(seed + 1 + a, n).reshape(ua.shape) for a, ua in enumerate(c.u)]
     return c
+
+
+def shock_tube_3d(shape=(768, 32, 32), Ma=1.15, shock_x=None, seed=None, rel=1e-3):
+    """D3Q27 planar shock tube of the learned-closure workload.
+
+    The post-shock state is that of the batch table's instance closest to
+    ``Ma`` (same vapour, units and parameters as shock_drop_d3q27); shock at
+    x = Nx/8; with ``seed`` a seeded perturbation of relative size ``rel``
+    (add_noise).  At Ma 1.15 the tube stays stable for 1000 steps; from Ma
+    ~1.2 a transverse instability of the front grows within 300 steps in
+    this scheme without shock capturing.
+    """
+    tab = scenario("batch_d2q9")["instances"]
+    k = min(range(len(tab)), key=lambda i: abs(tab[i]["Ma"] - Ma))
+    sc = dict(scenario("shock_drop_d3q27"))
+    sc["post"] = tab[k]["post"]
+    c = shock_drop(3, shape, shock_x=shape[0] // 8 if shock_x is None else shock_x, with_drop=False, sc=sc)
+    if seed is not None:
+        add_noise(c, seed, rel)
+    return c
+
+
+def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25):
+    """(case, e_scale) runs whose states train the learned closure.
+
+    The D2Q9 Riemann problem and ``n_tubes`` narrow D2Q9 shock tubes (shock
+    at Nx/4) whose post-shock states are spread over the batch table's Mach
+    numbers from 1.1 to Ma_max, all with a seeded 1e-3 perturbation.  The
+    tubes are a few nodes wide: wide planar shocks above Ma ~1.2 develop a
+    transverse instability within 1000 steps without shock capturing.
+    Energies are brought to the lattice units of the shock scenarios
+    (velocity scale squared U^2 = 12): e_scale = U^2(run) / U^2(shock) for
+    the Riemann problem.
+    """
+    tab = scenario("batch_d2q9")["instances"]
+    order = sorted((i for i in range(len(tab)) if tab[i]["Ma"] <= Ma_max), key=lambda i: tab[i]["Ma"])
+    pick = [order[int(round(j * (len(order) - 1) / max(n_tubes - 1, 1)))] for j in range(n_tubes)]
+    base = scenario("shock_drop_d2q9")
+    runs = [(add_noise(riemann(), seed), scenario("riemann_d2q9")["U2"] / base["U2"])]
+    for j, k in enumerate(pick):
+        sc = dict(base)
+        sc["post"] = tab[k]["post"]
+        c = shock_drop(2, (Nx, Ny), shock_x=Nx // 4, with_drop=False, sc=sc)
+        runs.append((add_noise(c, seed + 1 + 4 * j), 1.0))
+    return runs

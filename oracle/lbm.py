@@ -212,6 +212,10 @@ class Model:
         # Eq. qc: k/mu from the Prandtl number Pr = mu c_p / k at the reference state
         self.k_over_mu = thermo.cp(rho_ref, T_ref, self.a, self.b, self.R, self.cv) / float(Pr)
         self.x_low, self.x_high = x_low, x_high
+        # Optional thermodynamic closure (rho, e) -> (T, P, c_s^2) standing in
+        # for Eqs. lbm_temp, Pvdw and vdW_speed_of_sound (a learned closure);
+        # None: the exact van der Waals relations.
+        self.closure = None
         self.periodic_x = (x_low == "periodic")
         if (x_high == "periodic") != self.periodic_x:
             raise ValueError("x is periodic on both faces or on neither")
@@ -298,9 +302,13 @@ class Sim:
         uF = sum(u[a] * F[a] for a in range(D))
         E = (S + 0.5 * uF) / rho                                       # Eq. def_E
         usq = sum(ua * ua for ua in u)
-        T = thermo.temperature_from_energy(rho, E, usq, m.a, m.cv)    # Eq. lbm_temp
-        P = thermo.pressure(rho, T, m.a, m.b, m.R)                    # Eq. Pvdw
-        return dict(rho=rho, j=j, S=S, F=F, u=u, E=E, T=T, P=P, usq=usq, uF=uF)
+        if m.closure is None:
+            T = thermo.temperature_from_energy(rho, E, usq, m.a, m.cv)    # Eq. lbm_temp
+            P = thermo.pressure(rho, T, m.a, m.b, m.R)                    # Eq. Pvdw
+            return dict(rho=rho, j=j, S=S, F=F, u=u, E=E, T=T, P=P, usq=usq, uF=uF)
+        e = E - 0.5 * usq                                              # specific internal energy
+        T, P, cs2 = m.closure(rho, e)
+        return dict(rho=rho, j=j, S=S, F=F, u=u, E=E, T=T, P=P, usq=usq, uF=uF, e=e, cs2=cs2)
 
     # -- one time step -------------------------------------------------------
     def collide(self):
@@ -310,9 +318,12 @@ class Sim:
         q = self.macroscopic()
         rho, u, F, T, P = q["rho"], q["u"], q["F"], q["T"], q["P"]
         theta = P / rho                                                # Eq. theta
-        e = thermo.internal_energy(rho, T, m.a, m.cv)
+        if m.closure is None:
+            e = thermo.internal_energy(rho, T, m.a, m.cv)
+            cs2 = thermo.sound_speed_sq(rho, T, m.a, m.b, m.R, m.cv)  # Eq. vdW_speed_of_sound
+        else:
+            e, cs2 = q["e"], q["cs2"]
         h = e + P / rho                                                # Eq. enthalpy
-        cs2 = thermo.sound_speed_sq(rho, T, m.a, m.b, m.R, m.cv)      # Eq. vdW_speed_of_sound
         alpha = bulk_shift(D, rho, cs2, P, m.eta_over_mu)              # Eq. corr_bulk
         tau = m.mu / P                                                 # tau = mu / P
         beta = 1.0 / (2.0 * tau + 1.0)                                 # Eq. beta_main
@@ -326,8 +337,12 @@ class Sim:
         # step 5: shifted state
         ustar = [u[a] + F[a] / rho for a in range(D)]                  # Eq. sh_vel_1
         theta_s = theta + alpha * theta * div_u                        # Eq. sh_temp_1
-        T_s = shifted_temperature(T, F, rho, m.cv)                     # Eq. sh_T_1
-        e_s = thermo.internal_energy(rho, T_s, m.a, m.cv)
+        if m.closure is None:
+            T_s = shifted_temperature(T, F, rho, m.cv)                 # Eq. sh_T_1
+            e_s = thermo.internal_energy(rho, T_s, m.a, m.cv)
+        else:
+            # Eq. sh_T_1 in energy form (e linear in T at fixed rho): e* = e - |F|^2/(2 rho^2)
+            e_s = e - 0.5 * sum(F[a] * F[a] for a in range(D)) / (rho * rho)
         qc = heat_flux_correction(P, gradh, gradT, m.k_over_mu)        # Eq. qc_1
 
         # step 6: attractors

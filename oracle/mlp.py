@@ -160,3 +160,27 @@ def closure(theta, scale, rho, e, a, b, R, cv):
     net = [scale[4] + scale[5] * y[..., 0], scale[6] + scale[7] * y[..., 1], scale[8] + scale[9] * y[..., 2]]
     ex = vdw_targets(rho, e, a, b, R, cv)
     return tuple(np.where(used, n, x_) for n, x_ in zip(net, ex)) + (used,)
+
+
+def train(theta, X, Y, steps, batch, lr0, lr1, seed, wd=0.0):
+    """AdamW on minibatches of (X, Y) with the forward pass on quantize(theta).
+
+    The gradient of the rounded weights updates the full-precision master
+    weights (straight-through).  Minibatch k of step t holds the samples
+    floor((u + 1) n / 2) for the SplitMix64 values u of stream ``seed``
+    (inputs.uniform) from index t * batch; the learning rate falls from lr0
+    to lr1 along a half cosine.  Returns (theta, per-step losses).
+    """
+    import inputs
+    n = X.shape[0]
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    losses = []
+    for t in range(steps):
+        u = inputs.uniform(seed, batch, start=t * batch)
+        idx = np.minimum(((u + 1.0) * 0.5 * n).astype(np.int64), n - 1)
+        loss, g = loss_and_grad(quantize(theta), X[idx], Y[idx])
+        losses.append(loss)
+        lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * t / steps))
+        theta, m, v = adamw_step(theta, g, m, v, t + 1, lr, wd=wd)
+    return theta, np.array(losses)

@@ -36,7 +36,12 @@ EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_
            "lbm_batch_create", "lbm_batch_set_boundary", "lbm_batch_set_stream", "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_moments", "lbm_batch_flags",
            "lbm_batch_autotune", "lbm_batch_nodes", "lbm_batch_launch_count", "lbm_batch_destroy",
-           "lbm_batch_last_error")
+           "lbm_batch_last_error",
+           # include/lbm_mlp.h
+           "lbm_mlp_create", "lbm_mlp_set_stream", "lbm_mlp_collect", "lbm_mlp_fit_scaling", "lbm_mlp_get_scaling",
+           "lbm_mlp_set_scaling", "lbm_mlp_get_params", "lbm_mlp_set_params", "lbm_mlp_loss_grad", "lbm_mlp_train",
+           "lbm_mlp_predict", "lbm_mlp_attach", "lbm_get_closure", "lbm_mlp_destroy", "lbm_mlp_last_error")
+LBM_MLP_NPARAM, LBM_MLP_NSCALE = 4547, 10
 
 
 class LbmError(RuntimeError):
@@ -103,6 +108,21 @@ def load():
         "lbm_batch_launch_count": (ctypes.c_longlong, [P]),
         "lbm_batch_destroy": (I, [P]),
         "lbm_batch_last_error": (ctypes.c_char_p, []),
+        "lbm_mlp_create": (I, [ctypes.POINTER(P), D, D, D, D, ctypes.c_uint64]),
+        "lbm_mlp_set_stream": (I, [P, P]),
+        "lbm_mlp_collect": (I, [P, P, P, D]),
+        "lbm_mlp_fit_scaling": (I, [P, P, P, ctypes.c_longlong]),
+        "lbm_mlp_get_scaling": (I, [P, P]),
+        "lbm_mlp_set_scaling": (I, [P, P]),
+        "lbm_mlp_get_params": (I, [P, P]),
+        "lbm_mlp_set_params": (I, [P, P]),
+        "lbm_mlp_loss_grad": (I, [P, P, P, I, dp, P]),
+        "lbm_mlp_train": (I, [P, P, P, ctypes.c_longlong, I, I, D, D, D, ctypes.c_uint64, P]),
+        "lbm_mlp_predict": (I, [P, P, P, ctypes.c_longlong, P]),
+        "lbm_mlp_attach": (I, [P, P]),
+        "lbm_get_closure": (I, [P]),
+        "lbm_mlp_destroy": (I, [P]),
+        "lbm_mlp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -345,6 +365,98 @@ class Batch:
             pass
 
 
+# ---- learned closure (include/lbm_mlp.h) ----------------------------------------
+
+def _mcheck(rc):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_mlp_last_error().decode())
+    return rc
+
+
+def _f32(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    assert a.size == n
+    return a
+
+
+def lbm_mlp_create(a, b, R, cv, seed):
+    h = ctypes.c_void_p()
+    _mcheck(load().lbm_mlp_create(ctypes.byref(h), a, b, R, cv, ctypes.c_uint64(seed)))
+    return h
+
+
+def lbm_mlp_set_stream(net, stream_ptr):
+    _mcheck(load().lbm_mlp_set_stream(net, ctypes.c_void_p(stream_ptr)))
+
+
+def lbm_mlp_collect(h, rho, e, e_scale=1.0):
+    """Solver state -> (rho, e) samples in the device tensors rho, e (float64, Nx Ny Nz each)."""
+    _mcheck(load().lbm_mlp_collect(h, _dptr(rho), _dptr(e), e_scale))
+
+
+def lbm_mlp_fit_scaling(net, rho, e):
+    _mcheck(load().lbm_mlp_fit_scaling(net, _dptr(rho), _dptr(e), rho.numel()))
+
+
+def lbm_mlp_get_scaling(net):
+    s = np.zeros(LBM_MLP_NSCALE)
+    _mcheck(load().lbm_mlp_get_scaling(net, _ptr(s)))
+    return s
+
+
+def lbm_mlp_set_scaling(net, scale):
+    s = np.ascontiguousarray(scale, dtype=np.float64)
+    assert s.size == LBM_MLP_NSCALE
+    _mcheck(load().lbm_mlp_set_scaling(net, _ptr(s)))
+
+
+def lbm_mlp_get_params(net):
+    th = np.zeros(LBM_MLP_NPARAM, dtype=np.float32)
+    _mcheck(load().lbm_mlp_get_params(net, th.ctypes.data_as(ctypes.c_void_p)))
+    return th
+
+
+def lbm_mlp_set_params(net, theta):
+    th = _f32(theta, LBM_MLP_NPARAM)
+    _mcheck(load().lbm_mlp_set_params(net, th.ctypes.data_as(ctypes.c_void_p)))
+
+
+def lbm_mlp_loss_grad(net, x, y):
+    """(loss, gradient) of the network on host samples x (n, 2), y (n, 3)."""
+    n = int(np.asarray(x).shape[0])
+    xs, ys = _f32(x, 2 * n), _f32(y, 3 * n)
+    g = np.zeros(LBM_MLP_NPARAM, dtype=np.float32)
+    loss = ctypes.c_double()
+    _mcheck(load().lbm_mlp_loss_grad(net, xs.ctypes.data_as(ctypes.c_void_p), ys.ctypes.data_as(ctypes.c_void_p),
+                                     n, ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p)))
+    return loss.value, g
+
+
+def lbm_mlp_train(net, rho, e, batch, steps, lr0, lr1, wd=0.0, seed=0):
+    """AdamW steps on the device samples (rho, e); returns the per-step minibatch losses."""
+    losses = np.zeros(max(steps, 1), dtype=np.float32)
+    _mcheck(load().lbm_mlp_train(net, _dptr(rho), _dptr(e), rho.numel(), batch, steps, lr0, lr1, wd,
+                                 ctypes.c_uint64(seed), losses.ctypes.data_as(ctypes.c_void_p)))
+    return losses[:steps]
+
+
+def lbm_mlp_predict(net, rho, e, out):
+    """out (device float64, n x 4): T, P, c_s^2, network used (1) or exact (0)."""
+    _mcheck(load().lbm_mlp_predict(net, _dptr(rho), _dptr(e), rho.numel(), _dptr(out)))
+
+
+def lbm_mlp_attach(h, net):
+    _mcheck(load().lbm_mlp_attach(h, net))
+
+
+def lbm_get_closure(h):
+    return load().lbm_get_closure(h)
+
+
+def lbm_mlp_destroy(net):
+    return load().lbm_mlp_destroy(net)
+
+
 # ---- convenience wrapper -------------------------------------------------------
 
 class Solver:
@@ -393,5 +505,90 @@ class Solver:
         try:
             if self.h:
                 self.close()
+        except Exception:
+            pass
+
+
+# ---- learned closure wrapper ---------------------------------------------------
+
+class Closure:
+    """One learned-closure network (an lbm_mlp handle); device data are torch tensors."""
+
+    def __init__(self, a, b, R, cv, seed=1, stream=None):
+        self.eos = (a, b, R, cv)
+        self.net = lbm_mlp_create(a, b, R, cv, seed)
+        if stream:
+            lbm_mlp_set_stream(self.net, stream)
+
+    def collect(self, solver, e_scale=1.0):
+        """(rho, e) of the solver's current interior state as two device tensors."""
+        import torch
+        n = int(np.prod(solver.arr_shape))
+        rho = torch.empty(n, dtype=torch.float64, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        lbm_mlp_collect(solver.h, rho, e, e_scale)
+        return rho, e
+
+    def collect_runs(self, runs, snapshots, every, precision="fp64"):
+        """Run each (case, e_scale) for snapshots * every steps and collect every `every` steps."""
+        import torch
+        rs, es = [], []
+        for case, e_scale in runs:
+            s = Solver(case, precision).init()
+            for _ in range(snapshots):
+                s.step(every)
+                r, e = self.collect(s, e_scale)
+                rs.append(r)
+                es.append(e)
+            s.close()
+        return torch.cat(rs), torch.cat(es)
+
+    def fit_scaling(self, rho, e):
+        lbm_mlp_fit_scaling(self.net, rho, e)
+
+    @property
+    def scaling(self):
+        return lbm_mlp_get_scaling(self.net)
+
+    @scaling.setter
+    def scaling(self, s):
+        lbm_mlp_set_scaling(self.net, s)
+
+    @property
+    def params(self):
+        return lbm_mlp_get_params(self.net)
+
+    @params.setter
+    def params(self, theta):
+        lbm_mlp_set_params(self.net, theta)
+
+    def loss_grad(self, x, y):
+        return lbm_mlp_loss_grad(self.net, x, y)
+
+    def train(self, rho, e, batch=8192, steps=1000, lr0=3e-3, lr1=3e-5, wd=0.0, seed=0):
+        return lbm_mlp_train(self.net, rho, e, batch, steps, lr0, lr1, wd, seed)
+
+    def predict(self, rho, e):
+        """(n, 4) device tensor: T, P, c_s^2, 1 where the network was used."""
+        import torch
+        out = torch.empty((rho.numel(), 4), dtype=torch.float64, device="cuda")
+        lbm_mlp_predict(self.net, rho, e, out)
+        return out
+
+    def attach(self, solver):
+        lbm_mlp_attach(solver.h, self.net)
+
+    @staticmethod
+    def detach(solver):
+        lbm_mlp_attach(solver.h, None)
+
+    def close(self):
+        if self.net:
+            lbm_mlp_destroy(self.net)
+        self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

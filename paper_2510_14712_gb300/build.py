@@ -35,7 +35,7 @@ def _stale(srcs):
         return True
     t = os.path.getmtime(LIB)
     deps = srcs + [os.path.join(SRC, f) for f in os.listdir(SRC)] + \
-        [os.path.join(HERE, "..", "include", "lbm.h"), os.path.abspath(__file__)]
+        [os.path.join(HERE, "..", "include", f) for f in ("lbm.h", "lbm_mlp.h")] + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

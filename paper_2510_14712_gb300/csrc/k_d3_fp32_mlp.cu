@@ -1,0 +1,11 @@
+// Fused step with the learned closure: D = 3, storage float, arithmetic float.
+#include "lbm_ops.cuh"
+
+namespace lbm {
+void step_d3_fp32_mlp(Handle& h, const void* src, void* dst) {
+  OpsImpl<3, float, float>::step_cl<MlpClosure>(h, src, dst);
+}
+int autotune_d3_fp32_mlp(Handle& h, int reps, float* best_ms) {
+  return OpsImpl<3, float, float>::autotune_cl<MlpClosure>(h, reps, best_ms);
+}
+}  // namespace lbm

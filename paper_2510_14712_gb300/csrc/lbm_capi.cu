@@ -41,7 +41,25 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// Exact-closure table with the fused step and the autotuner swapped for the
+// learned-closure ones (multi-pass and batched steps are exact-only).
+Ops with_mlp(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*)) {
+  Ops o = *base;
+  o.step = step;
+  o.autotune = tune;
+  o.step_multipass = nullptr;
+  o.batch_ncfg = nullptr;
+  o.batch_prepare = nullptr;
+  o.batch_enqueue = nullptr;
+  return o;
+}
+
 const Ops* ops_for(const Handle& h) {
+  if (h.closure == LBM_CLOSURE_MLP) {
+    static const Ops m2 = with_mlp(ops_d2_fp32(), step_d2_fp32_mlp, autotune_d2_fp32_mlp);
+    static const Ops m3 = with_mlp(ops_d3_fp32(), step_d3_fp32_mlp, autotune_d3_fp32_mlp);
+    return h.D == 2 ? &m2 : &m3;
+  }
   if (h.D == 2) {
     if (h.precision == LBM_FP64) return ops_d2_fp64();
     if (h.precision == LBM_FP32) return ops_d2_fp32();
@@ -115,9 +133,10 @@ void set_face_eq(Handle& h, int face) {
 }
 
 // Autotune results of this process, keyed by lattice, precision and padded
-// geometry: a new handle of the same shape starts with the tuned tile.
+// geometry and closure: a new handle of the same shape starts with the tuned
+// tile.
 struct TuneEntry {
-  int Q, precision, Nx, Ny, Nz, periodic_x, cfg;
+  int Q, precision, Nx, Ny, Nz, periodic_x, closure, cfg;
 };
 TuneEntry g_tuned[32];
 int g_ntuned = 0;
@@ -128,7 +147,7 @@ int tuned_cfg(const Handle& h) {
   for (int k = 0; k < g_ntuned; ++k) {
     const TuneEntry& e = g_tuned[k];
     if (e.Q == h.Q && e.precision == h.precision && e.Nx == h.Nx && e.Ny == h.Ny && e.Nz == h.Nz &&
-        e.periodic_x == h.p.periodic_x)
+        e.periodic_x == h.p.periodic_x && e.closure == h.closure)
       return e.cfg;
   }
   return 0;
@@ -139,12 +158,12 @@ void remember_cfg(const Handle& h) {
   for (int k = 0; k < g_ntuned; ++k) {
     TuneEntry& e = g_tuned[k];
     if (e.Q == h.Q && e.precision == h.precision && e.Nx == h.Nx && e.Ny == h.Ny && e.Nz == h.Nz &&
-        e.periodic_x == h.p.periodic_x) {
+        e.periodic_x == h.p.periodic_x && e.closure == h.closure) {
       e.cfg = h.tile_cfg;
       return;
     }
   }
-  if (g_ntuned < 32) g_tuned[g_ntuned++] = {h.Q, h.precision, h.Nx, h.Ny, h.Nz, h.p.periodic_x, h.tile_cfg};
+  if (g_ntuned < 32) g_tuned[g_ntuned++] = {h.Q, h.precision, h.Nx, h.Ny, h.Nz, h.p.periodic_x, h.closure, h.tile_cfg};
 }
 
 int read_err(Handle& h) {
@@ -177,7 +196,8 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
   if (!(eos->rho_ref > 0) || !(eos->T_ref > 0) || !(eos->b * eos->rho_ref < 1) || !(eos->R > 0))
     return fail(LBM_EINVAL, "need rho_ref > 0, T_ref > 0, R > 0, b rho_ref < 1");
   if (eos->precision < LBM_FP64 || eos->precision > LBM_FP16DEV) return fail(LBM_EINVAL, "bad precision");
-  if (eos->closure != LBM_CLOSURE_EXACT) return fail(LBM_EINVAL, "closure not supported by this build");
+  if (eos->closure != LBM_CLOSURE_EXACT)
+    return fail(LBM_EINVAL, "create with LBM_CLOSURE_EXACT; a learned closure is attached by lbm_mlp_attach");
   if ((long long)Nx * Ny * Nz > (1LL << 31)) return fail(LBM_EINVAL, "too many nodes");
 
   lbm_s* h = new (std::nothrow) lbm_s();
@@ -308,6 +328,7 @@ int lbm_step_async(lbm_t h, int n) {
   if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
   const Ops* o = ops_for(*h);
   auto fn = h->step_kernel == LBM_STEP_MULTIPASS ? o->step_multipass : o->step;
+  if (!fn) return fail(LBM_EINVAL, "the learned closure runs in the fused step only");
   for (int k = 0; k < n; ++k) {
     fn(*h, h->pop[h->cur], h->pop[h->cur ^ 1]);
     h->cur ^= 1;
@@ -409,6 +430,7 @@ long long lbm_launch_count(lbm_t h) { return h ? h->launches : 0; }
 int lbm_destroy(lbm_t h) {
   if (!h) return LBM_OK;
   free_state(*h);
+  if (h->mlp_img) cudaFree(h->mlp_img);
   if (h->partials) cudaFree(h->partials);
   if (h->totals_dev) cudaFree(h->totals_dev);
   if (h->err_dev) cudaFree(h->err_dev);

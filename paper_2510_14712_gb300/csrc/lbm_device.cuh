@@ -127,9 +127,11 @@ template <int D, typename real> struct NodeFields {
   real u[D], T, h, Lam[D];
 };
 
-// Inputs of the collision at one node besides the populations.
+// Inputs of the collision at one node besides the populations.  T, P, c_s^2
+// come from the thermodynamic closure of the node (exact vdW or learned) and
+// e is the specific internal energy.
 template <int D, typename real> struct NodeState {
-  real rho, u[D], F[D], T;
+  real rho, u[D], F[D], T, P, cs2, e;
   real div_u;            // central divergence of u
   real gradT[D], gradh[D];
   real dLam[D];          // upwind derivative of Lambda_a along a (Sec. 3.2)
@@ -151,10 +153,10 @@ template <int D, typename real> struct Attractors {
     rho = s.rho;
     const real T = s.T;
     const real inv_rho = real(1) / rho;
-    const real P = vdw_pressure(m, rho, T);
+    const real P = s.P;
     const real theta = P * inv_rho;                                        // Eq. theta
-    e = vdw_energy(m, rho, T);
-    const real cs2 = vdw_cs2(m, rho, T);
+    e = s.e;
+    const real cs2 = s.cs2;
     const real alpha = real(D + 2) / real(D) - rho * cs2 / P - m.eta_over_mu;   // Eq. corr_bulk
     const real tau = m.mu / P;                                             // tau = mu / P
     const real beta = real(1) / (real(2) * tau + real(1));                 // Eq. beta_main
@@ -168,8 +170,9 @@ template <int D, typename real> struct Attractors {
       FF += s.F[a] * s.F[a];
     }
     const real theta_s = theta + alpha * theta * s.div_u;
-    const real T_s = T - FF * real(0.5) * inv_rho * inv_rho / m.cv;
-    e_s = vdw_energy(m, rho, T_s);
+    // T* = T - |F|^2 / (2 rho^2 c_v): with e linear in T at fixed rho this is
+    // e* = e - |F|^2 / (2 rho^2)
+    e_s = e - FF * real(0.5) * inv_rho * inv_rho;
 #pragma unroll
     for (int a = 0; a < D; ++a) qc[a] = P * (s.gradh[a] - m.k_over_mu * s.gradT[a]);
 #pragma unroll

@@ -3,7 +3,8 @@
 // One kernel does, for every interior node, everything of Sec. 3.2 between
 // reading the post-collision populations of the last step and writing the
 // new ones: pull-stream, moments (Eqs. def_h, def_u, def_E), Korteweg force
-// (Eq. FK), EOS and temperature (Eqs. Pvdw, lbm_temp), neighbour derivatives
+// (Eq. FK), closure: temperature, EOS, sound speed (Eqs. lbm_temp, Pvdw,
+// vdW_speed_of_sound; exact or learned), neighbour derivatives
 // (central; upwind for Phi), shifted state, attractors and collision (Eqs.
 // fLBGK, gLBGK).  The ghost layers of non-periodic x faces are refilled by
 // the separate k_ghosts kernel afterwards.
@@ -24,20 +25,63 @@
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "lbm_mlp.cuh"
 
 namespace lbm {
 
-template <int D, int TX, int TY> struct FusedGeom {
+// EX: extra per-node fields of the primitive ring (2 when the closure's P and
+// c_s^2 are stored for the collision instead of recomputed there).
+template <int D, int TX, int TY, int EX = 0> struct FusedGeom {
   static constexpr int NT = TX * TY;                 // threads per CTA
   static constexpr int HY3 = D == 3 ? 3 : 0, HY2 = D == 3 ? 2 : 0, HY1 = D == 3 ? 1 : 0;
   static constexpr int BX3 = TX + 6, BY3 = TY + 2 * HY3, N3 = BX3 * BY3;
   static constexpr int BX2 = TX + 4, BY2 = TY + 2 * HY2, N2 = BX2 * BY2;
   static constexpr int BX1 = TX + 2, BY1 = TY + 2 * HY1, N1 = BX1 * BY1;
   static constexpr int NMOM = D + 1;                 // j_0..j_{D-1}, S
-  static constexpr int NPRIM = 3 * D + 4;            // rho, u[D], T, h, Lam[D], F[D]
+  static constexpr int NPRIM = 3 * D + 4 + EX;       // rho, u[D], T, h, Lam[D], F[D] (, P, c_s^2)
   static constexpr int P_RHO = 0, P_U = 1, P_T = 1 + D, P_H = 2 + D, P_LAM = 3 + D, P_F = 3 + 2 * D;
+  static constexpr int P_P = 3 + 3 * D, P_CS2 = 4 + 3 * D;
+  // bytes of the four rings, rounded up to 16 (a closure's table follows them)
   template <typename real> static constexpr size_t smem_bytes() {
-    return sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1);
+    return (sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1) + 15) & ~size_t(15);
+  }
+};
+
+// Thermodynamic closures (rho, e) -> (T, P, c_s^2) used by stage C of the
+// fused step.  kWarp: the closure is warp-collective (every lane calls it,
+// `act` says whether the lane's node is real).  kExtra: fields the closure
+// adds to the primitive ring.  kSmem: shared-memory table bytes it loads.
+
+// Exact van der Waals closure: Eqs. lbm_temp (with e = E - u^2/2), Pvdw,
+// vdW_speed_of_sound.
+template <typename real> struct ExactClosure {
+  static constexpr bool kWarp = false;
+  static constexpr int kExtra = 0;
+  static constexpr size_t kSmem = 0;
+  __device__ __forceinline__ void load(const Params&, unsigned char*) {}
+  __device__ __forceinline__ void operator()(const Model<real>& m, real rho, real e, bool, real& T, real& P,
+                                             real& cs2) const {
+    T = (e + m.a * rho) / m.cv;
+    P = vdw_pressure(m, rho, T);
+    cs2 = vdw_cs2(m, rho, T);
+  }
+};
+
+// Learned closure: the network of lbm_mlp.cuh inside its training box, the
+// exact closure outside it (range gate).  FP32 arithmetic only.
+struct MlpClosure {
+  static constexpr bool kWarp = true;
+  static constexpr int kExtra = 2;
+  static constexpr size_t kSmem = sizeof(mlp::Image);
+  const mlp::Image* w;
+  __device__ __forceinline__ void load(const Params& p, unsigned char* smem) {
+    mlp::Image* d = reinterpret_cast<mlp::Image*>(smem);
+    mlp::load_image(static_cast<const mlp::Image*>(p.mlp), d);
+    w = d;
+  }
+  __device__ __forceinline__ void operator()(const Model<float>& m, float rho, float e, bool act, float& T, float& P,
+                                             float& cs2) const {
+    mlp::closure_warp(*w, m, rho, e, act, T, P, cs2);
   }
 };
 
@@ -65,12 +109,12 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
 // single-instance kernel and the batched persistent kernel.  SMALL: the box
 // is narrower than a tile plus its halo in x or y, so coordinates need an
 // exact modulo instead of a single conditional wrap.
-template <int D, typename S, typename real, int TX, int TY, bool SMALL>
+template <int D, typename S, typename real, int TX, int TY, bool SMALL, class CL>
 __device__ __forceinline__ void fused_column(const Params& p, const typename Store<S>::T* __restrict__ A,
                                              typename Store<S>::T* __restrict__ B, int x0, int y0, int mb, int me,
-                                             unsigned char* smem_raw, unsigned& flags) {
+                                             unsigned char* smem_raw, unsigned& flags, const CL& closure) {
   using L = Lattice<D>;
-  using G = FusedGeom<D, TX, TY>;
+  using G = FusedGeom<D, TX, TY, CL::kExtra>;
   constexpr int Q = L::Q;
   real* s_rho = reinterpret_cast<real*>(smem_raw);            // [3][N3]
   real* s_mom = s_rho + 3 * G::N3;                            // [3][NMOM][N1]
@@ -174,44 +218,60 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     __syncthreads();
 
     // ---------------- C: primitive fields, plane pl-2, on R1 ------------------
+    // The loop runs a warp-uniform number of times (warp-collective closures);
+    // `act` marks the lanes whose position is a needed node.
     if (pl - 2 >= mb - 1) {
       const int q = pl - 2;
       const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
-      for (int k = tid; k < G::N1; k += G::NT) {
+      const int lane = tid & 31;
+      for (int k0 = tid - lane; k0 < G::N1; k0 += G::NT) {
+        const int k = k0 + lane;
         const int lx = k % G::BX1, ly = k / G::BX1;
         const int ox = outside(lx, 1, TX), oy = D == 3 ? outside(ly, G::HY1, TY) : 0;
-        if (ox + oy > 1) continue;
         const int gx = x0 + lx - 1;
-        if (gx < xmin + 2 || gx > xmax - 2) continue;
-        const int k3 = (ly + (G::HY3 - G::HY1)) * G::BX3 + (lx + 2);
-        const int k2 = (ly + (G::HY2 - G::HY1)) * G::BX2 + (lx + 1);
-        const real rho = s_rho[sc * G::N3 + k3];
-        const real* lp = s_lap + sc * G::N2;
-        real F[D];
-        F[0] = m.kappa * rho * real(0.5) * (lp[k2 + 1] - lp[k2 - 1]);                         // Eq. FK
-        if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
-        F[D - 1] = m.kappa * rho * real(0.5) * (s_lap[sp * G::N2 + k2] - s_lap[sm * G::N2 + k2]);
-        const real* mo = s_mom + (sc * G::NMOM) * G::N1 + k;
-        real u[D], uF = 0, u2 = 0;
+        const bool act = k < G::N1 && ox + oy <= 1 && gx >= xmin + 2 && gx <= xmax - 2;
+        real rho = real(1), e = real(0), F[D], u[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          u[a] = (mo[a * G::N1] + real(0.5) * F[a]) / rho;                                     // Eq. def_u
-          uF += u[a] * F[a];
-          u2 += u[a] * u[a];
+        for (int a = 0; a < D; ++a) F[a] = u[a] = real(0);
+        if (act) {
+          const int k3 = (ly + (G::HY3 - G::HY1)) * G::BX3 + (lx + 2);
+          const int k2 = (ly + (G::HY2 - G::HY1)) * G::BX2 + (lx + 1);
+          rho = s_rho[sc * G::N3 + k3];
+          const real* lp = s_lap + sc * G::N2;
+          F[0] = m.kappa * rho * real(0.5) * (lp[k2 + 1] - lp[k2 - 1]);                         // Eq. FK
+          if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
+          F[D - 1] = m.kappa * rho * real(0.5) * (s_lap[sp * G::N2 + k2] - s_lap[sm * G::N2 + k2]);
+          const real* mo = s_mom + (sc * G::NMOM) * G::N1 + k;
+          real uF = 0, u2 = 0;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            u[a] = (mo[a * G::N1] + real(0.5) * F[a]) / rho;                                   // Eq. def_u
+            uF += u[a] * F[a];
+            u2 += u[a] * u[a];
+          }
+          const real E = (mo[D * G::N1] + real(0.5) * uF) / rho;                              // Eq. def_E
+          e = E - real(0.5) * u2;
         }
-        const real E = (mo[D * G::N1] + real(0.5) * uF) / rho;                                // Eq. def_E
-        const real T = (E - real(0.5) * u2 + m.a * rho) / m.cv;                                 // Eq. lbm_temp
-        const real P = vdw_pressure(m, rho, T);
-        const real theta = P / rho;
-        real* pr = s_prm + (sc * G::NPRIM) * G::N1 + k;
-        pr[G::P_RHO * G::N1] = rho;
-        pr[G::P_T * G::N1] = T;
-        pr[G::P_H * G::N1] = vdw_energy(m, rho, T) + theta;                                   // Eq. enthalpy
+        // closure (rho, e) -> (T, P, c_s^2)
+        real T = real(0), P = real(1), cs2 = real(0);
+        if constexpr (CL::kWarp) closure(m, rho, e, act, T, P, cs2);
+        else if (act) closure(m, rho, e, act, T, P, cs2);
+        if (act) {
+          const real theta = P / rho;
+          real* pr = s_prm + (sc * G::NPRIM) * G::N1 + k;
+          pr[G::P_RHO * G::N1] = rho;
+          pr[G::P_T * G::N1] = T;
+          pr[G::P_H * G::N1] = e + theta;                                                      // Eq. enthalpy
+          if constexpr (CL::kExtra > 0) {
+            pr[G::P_P * G::N1] = P;
+            pr[G::P_CS2 * G::N1] = cs2;
+          }
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          pr[(G::P_U + a) * G::N1] = u[a];
-          pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
-          pr[(G::P_F + a) * G::N1] = F[a];
+          for (int a = 0; a < D; ++a) {
+            pr[(G::P_U + a) * G::N1] = u[a];
+            pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
+            pr[(G::P_F + a) * G::N1] = F[a];
+          }
         }
       }
     }
@@ -241,6 +301,15 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
         NodeState<D, real> s;
         s.rho = pc[G::P_RHO * G::N1 + k1];
         s.T = pc[G::P_T * G::N1 + k1];
+        if constexpr (CL::kExtra > 0) {
+          s.P = pc[G::P_P * G::N1 + k1];
+          s.cs2 = pc[G::P_CS2 * G::N1 + k1];
+          s.e = pc[G::P_H * G::N1 + k1] - s.P / s.rho;
+        } else {
+          s.P = vdw_pressure(m, s.rho, s.T);
+          s.cs2 = vdw_cs2(m, s.rho, s.T);
+          s.e = vdw_energy(m, s.rho, s.T);
+        }
         s.div_u = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -300,11 +369,16 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 // columns at the same planes and their halos are L2 hits.  MINB: CTAs per SM
 // the register allocation must allow (2 keeps one CTA's memory phase
 // overlapping the other's collision).
-template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL>
+template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL, class CL = ExactClosure<real>>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __restrict__ A,
              typename Store<S>::T* __restrict__ B, unsigned* err, int ncolx, int ncoly, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  CL closure;
+  if constexpr (CL::kSmem > 0) {
+    closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra>::template smem_bytes<real>());
+    __syncthreads();
+  }
   unsigned flags = 0;
   const int Nm = D == 3 ? p.Nz : p.Ny;
   const int ncol = ncolx * ncoly;
@@ -315,7 +389,7 @@ k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __res
     const int mb = int((long long)Nm * seg / nseg), me = int((long long)Nm * (seg + 1) / nseg);
     const int x0 = (col % ncolx) * TX;
     const int y0 = D == 3 ? (col / ncolx) * TY : 0;
-    fused_column<D, S, real, TX, TY, SMALL>(p, A, B, x0, y0, mb, me, smem_raw, flags);
+    fused_column<D, S, real, TX, TY, SMALL, CL>(p, A, B, x0, y0, mb, me, smem_raw, flags, closure);
   }
   if (flags) atomicOr(err, flags);
 }
@@ -361,8 +435,9 @@ k_step_fused_batch(const BatchInstance* __restrict__ insts, const BatchItem* __r
     const int y0 = D == 3 ? (w.col / bi.ncolx) * TY : 0;
     unsigned flags = 0;
     const bool small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
-    if (small) fused_column<D, S, real, TX, TY, true>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags);
-    else fused_column<D, S, real, TX, TY, false>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags);
+    const ExactClosure<real> cl{};
+    if (small) fused_column<D, S, real, TX, TY, true>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags, cl);
+    else fused_column<D, S, real, TX, TY, false>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags, cl);
     if (flags) atomicOr(errs + w.inst, flags);
   }
 }

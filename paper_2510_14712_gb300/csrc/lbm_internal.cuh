@@ -30,6 +30,8 @@ struct Params {
   double eq_lo[54], eq_hi[54];   // f then g
   // FP16-deviation reference populations (f then g)
   float ref[54];
+  // learned closure: device inference image (mlp::Image), NULL for the exact closure
+  const void* mlp;
 };
 
 template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
@@ -63,6 +65,8 @@ struct Handle {
   int step_kernel;            // LBM_STEP_FUSED | LBM_STEP_MULTIPASS
   int tile_cfg;               // index of the fused kernel's tile shape (lbm_autotune)
   long long launches;
+  int closure;                // LBM_CLOSURE_EXACT | LBM_CLOSURE_MLP
+  void* mlp_img;              // device copy of the attached network's inference image
 };
 
 struct Batch;
@@ -119,5 +123,10 @@ const Ops* ops_d3_fp64();
 const Ops* ops_d3_fp32();
 const Ops* ops_d2_fp16();
 const Ops* ops_d3_fp16();
+// fused step and tile autotuner with the learned closure (FP32 storage)
+void step_d2_fp32_mlp(Handle& h, const void* src, void* dst);
+void step_d3_fp32_mlp(Handle& h, const void* src, void* dst);
+int autotune_d2_fp32_mlp(Handle& h, int reps, float* best_ms);
+int autotune_d3_fp32_mlp(Handle& h, int reps, float* best_ms);
 
 }  // namespace lbm

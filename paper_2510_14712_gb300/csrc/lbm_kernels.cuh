@@ -270,6 +270,9 @@ __global__ void k_collide(Params p, const typename Store<S>::T* A, typename Stor
   NodeState<D, real> s;
   s.rho = M[o];
   s.T = W[D * p.plane + o];
+  s.P = vdw_pressure(m, s.rho, s.T);
+  s.cs2 = vdw_cs2(m, s.rho, s.T);
+  s.e = vdw_energy(m, s.rho, s.T);
   s.div_u = 0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {

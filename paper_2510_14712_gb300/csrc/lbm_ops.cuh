@@ -39,9 +39,10 @@ template <int D, typename S, typename real> struct OpsImpl {
   }
 
   // One tile shape of the fused kernel (TX x TY in-plane nodes, MINB CTAs
-  // per SM for the register budget).
-  template <int TX, int TY, int MINB> struct Fused {
-    using FG = FusedGeom<D, TX, TY>;
+  // per SM for the register budget) with thermodynamic closure CL.
+  template <int TX, int TY, int MINB, class CL> struct Fused {
+    using FG = FusedGeom<D, TX, TY, CL::kExtra>;
+    static size_t smem() { return FG::template smem_bytes<real>() + CL::kSmem; }
     struct Launch {
       int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
       bool small = false;
@@ -51,13 +52,12 @@ template <int D, typename S, typename real> struct OpsImpl {
     // segment), and never more items than slots so that all run together.
     static Launch plan(const Params& p) {
       static int blocks_per_sm = -1, sms = 0;
-      const size_t smem = FG::template smem_bytes<real>();
       if (blocks_per_sm < 0) {
-        auto kern = k_step_fused<D, S, real, TX, TY, MINB, false>;
-        auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        cudaFuncSetAttribute(kern_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem);
+        auto kern = k_step_fused<D, S, real, TX, TY, MINB, false, CL>;
+        auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true, CL>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        cudaFuncSetAttribute(kern_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem());
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -82,9 +82,10 @@ template <int D, typename S, typename real> struct OpsImpl {
     static void launch(Handle& h, const void* src, void* dst) {
       const Params& p = h.p;
       const Launch l = plan(p);
-      auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true> : k_step_fused<D, S, real, TX, TY, MINB, false>;
-      kern<<<l.grid, FG::NT, FG::template smem_bytes<real>(), h.stream>>>(
-          p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst), h.err_dev, l.ncolx, l.ncoly, l.nseg);
+      auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true, CL>
+                          : k_step_fused<D, S, real, TX, TY, MINB, false, CL>;
+      kern<<<l.grid, FG::NT, smem(), h.stream>>>(p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst),
+                                                 h.err_dev, l.ncolx, l.ncoly, l.nseg);
       h.launches += 1;
     }
   };
@@ -92,20 +93,31 @@ template <int D, typename S, typename real> struct OpsImpl {
   // Candidate tile shapes, first = default.  FP64 keeps one shape (its
   // arithmetic, not the tile, bounds it).
   using LaunchFn = void (*)(Handle&, const void*, void*);
-  static int candidates(const LaunchFn** fns) {
-    if (D == 3) {
-      if (sizeof(real) == 8) {
-        static const LaunchFn c[] = {&Fused<32, 8, 1>::launch};
+  // The learned closure adds a register-hungry network evaluation to stage C,
+  // so its list also offers the unrestricted (MINB 1) allocation.
+  template <class CL> static int candidates(const LaunchFn** fns) {
+    if constexpr (D == 3) {
+      if constexpr (sizeof(real) == 8) {
+        static const LaunchFn c[] = {&Fused<32, 8, 1, CL>::launch};
         *fns = c;
         return 1;
+      } else if constexpr (CL::kWarp) {
+        static const LaunchFn c[] = {&Fused<32, 8, 2, CL>::launch, &Fused<32, 8, 1, CL>::launch,
+                                     &Fused<32, 16, 1, CL>::launch};
+        *fns = c;
+        return 3;
+      } else {
+        static const LaunchFn c[] = {&Fused<32, 8, 2, CL>::launch, &Fused<32, 16, 1, CL>::launch,
+                                     &Fused<16, 16, 2, CL>::launch};
+        *fns = c;
+        return 3;
       }
-      static const LaunchFn c[] = {&Fused<32, 8, 2>::launch, &Fused<32, 16, 1>::launch, &Fused<16, 16, 2>::launch};
+    } else {
+      static const LaunchFn c[] = {&Fused<256, 1, 2, CL>::launch, &Fused<128, 1, 4, CL>::launch,
+                                   &Fused<512, 1, 1, CL>::launch};
       *fns = c;
       return 3;
     }
-    static const LaunchFn c[] = {&Fused<256, 1, 2>::launch, &Fused<128, 1, 4>::launch, &Fused<512, 1, 1>::launch};
-    *fns = c;
-    return 3;
   }
 
   static void ghosts(Handle& h, void* dst) {
@@ -116,18 +128,19 @@ template <int D, typename S, typename real> struct OpsImpl {
     }
   }
 
-  static void step(Handle& h, const void* src, void* dst) {
+  template <class CL> static void step_cl(Handle& h, const void* src, void* dst) {
     const LaunchFn* fns;
-    const int n = candidates(&fns);
+    const int n = candidates<CL>(&fns);
     fns[h.tile_cfg < n ? h.tile_cfg : 0](h, src, dst);
     ghosts(h, dst);
   }
+  static void step(Handle& h, const void* src, void* dst) { step_cl<ExactClosure<real>>(h, src, dst); }
 
   // Time every candidate shape for `reps` steps from the current state into
   // the spare buffer (the state is not advanced) and keep the fastest.
-  static int autotune(Handle& h, int reps, float* best_ms) {
+  template <class CL> static int autotune_cl(Handle& h, int reps, float* best_ms) {
     const LaunchFn* fns;
-    const int n = candidates(&fns);
+    const int n = candidates<CL>(&fns);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -154,6 +167,7 @@ template <int D, typename S, typename real> struct OpsImpl {
     if (best_ms) *best_ms = bt / (reps > 0 ? reps : 1);
     return best;
   }
+  static int autotune(Handle& h, int reps, float* best_ms) { return autotune_cl<ExactClosure<real>>(h, reps, best_ms); }
 
   static void step_multipass(Handle& h, const void* src, void* dst) {
     const Params& p = h.p;
@@ -241,24 +255,26 @@ template <int D, typename S, typename real> struct OpsImpl {
   using PrepFn = int (*)(Batch&);
   using EnqFn = void (*)(Batch&, int);
   static int batch_cands(const PrepFn** pf, const EnqFn** ef) {
-    if (D == 3) {
-      if (sizeof(real) == 8) {
+    if constexpr (D == 3) {
+      if constexpr (sizeof(real) == 8) {
         static const PrepFn p[] = {&BatchFused<32, 8, 1>::prepare};
         static const EnqFn e[] = {&BatchFused<32, 8, 1>::enqueue};
         *pf = p; *ef = e;
         return 1;
+      } else {
+        static const PrepFn p[] = {&BatchFused<32, 8, 2>::prepare, &BatchFused<16, 16, 2>::prepare};
+        static const EnqFn e[] = {&BatchFused<32, 8, 2>::enqueue, &BatchFused<16, 16, 2>::enqueue};
+        *pf = p; *ef = e;
+        return 2;
       }
-      static const PrepFn p[] = {&BatchFused<32, 8, 2>::prepare, &BatchFused<16, 16, 2>::prepare};
-      static const EnqFn e[] = {&BatchFused<32, 8, 2>::enqueue, &BatchFused<16, 16, 2>::enqueue};
+    } else {
+      static const PrepFn p[] = {&BatchFused<256, 1, 2>::prepare, &BatchFused<128, 1, 4>::prepare,
+                                 &BatchFused<64, 1, 8>::prepare};
+      static const EnqFn e[] = {&BatchFused<256, 1, 2>::enqueue, &BatchFused<128, 1, 4>::enqueue,
+                                &BatchFused<64, 1, 8>::enqueue};
       *pf = p; *ef = e;
-      return 2;
+      return 3;
     }
-    static const PrepFn p[] = {&BatchFused<256, 1, 2>::prepare, &BatchFused<128, 1, 4>::prepare,
-                               &BatchFused<64, 1, 8>::prepare};
-    static const EnqFn e[] = {&BatchFused<256, 1, 2>::enqueue, &BatchFused<128, 1, 4>::enqueue,
-                              &BatchFused<64, 1, 8>::enqueue};
-    *pf = p; *ef = e;
-    return 3;
   }
   static int batch_ncfg() {
     const PrepFn* pf;

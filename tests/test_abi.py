@@ -21,9 +21,13 @@ def lib():
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names.update(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_expected_entry_points():
@@ -71,3 +75,17 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_mlp_invalid_arguments_rejected_without_gpu(lib):
+    import paper_2510_14712_gb300 as P
+    h = ctypes.c_void_p()
+    assert lib.lbm_mlp_create(None, 0.25, 1 / 3, 8 / 3, 8.0, 1) == P.LBM_EINVAL
+    assert lib.lbm_mlp_create(ctypes.byref(h), 0.25, 1 / 3, -1.0, 8.0, 1) == P.LBM_EINVAL
+    assert b"R > 0" in lib.lbm_mlp_last_error()
+    assert lib.lbm_mlp_set_scaling(None, None) == P.LBM_EINVAL
+    assert lib.lbm_mlp_attach(None, None) == P.LBM_EINVAL
+    assert lib.lbm_mlp_loss_grad(None, None, None, 1, None, None) == P.LBM_EINVAL
+    assert lib.lbm_mlp_train(None, None, None, 1, 64, 1, 1e-3, 1e-4, 0.0, 0, None) == P.LBM_EINVAL
+    assert lib.lbm_get_closure(None) == P.LBM_CLOSURE_EXACT
+    assert lib.lbm_mlp_destroy(None) == P.LBM_OK

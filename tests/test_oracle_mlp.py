@@ -110,3 +110,36 @@ def test_training_reduces_loss():
         _, g = mlp.loss_and_grad(theta, X, Y)
         theta, m, v = mlp.adamw_step(theta, g, m, v, t, lr=3e-3)
     assert mlp.loss_and_grad(theta, X, Y)[0] < 0.05 * l0
+
+
+def test_oracle_closure_hook_with_exact_relations_reproduces_the_exact_step():
+    """The Model closure hook, fed the exact relations, gives the standard step (round-off)."""
+    from oracle import lbm
+    import mlp_util
+    a, b, R, cv = mlp_util.shock_eos()
+    c = mlp_util.shock_tube(2, (96, 3))
+    runs = []
+    for hook in (None, lambda rho, e: mlp.vdw_targets(rho, e, a, b, R, cv)):
+        m = lbm.Model(c.D, c.shape, c.eos, c.tau, c.Pr, c.cv, c.x_low, c.x_high)
+        m.closure = hook
+        s = lbm.Sim(m, c.rho, c.u, c.T)
+        s.step(40)
+        runs.append(s.fields())
+    for k in ("rho", "T"):
+        assert np.allclose(runs[0][k], runs[1][k], rtol=1e-12, atol=0)
+    assert np.allclose(runs[0]["u"], runs[1]["u"], rtol=0, atol=1e-13)
+
+
+def test_oracle_training_fits_the_closure():
+    """The oracle's own AdamW loop fits the closure on its box (normalised RMS < 2e-2)."""
+    import mlp_util
+    theta, scale, losses = mlp_util.oracle_network(steps=600)
+    assert losses[-50:].mean() < 0.02 * losses[:10].mean()
+    a, b, R, cv = mlp_util.shock_eos()
+    rho = 0.385 + 0.1 * inputs.uniform(99, 500)
+    T = 0.105 + 0.018 * inputs.uniform(98, 500)
+    e = cv * T - a * rho
+    Tn, Pn, cn, used = mlp.closure(mlp.quantize(theta), scale, rho, e, a, b, R, cv)
+    Te, Pe, ce = mlp.vdw_targets(rho, e, a, b, R, cv)
+    assert used.all()
+    assert np.sqrt(np.mean(((Pn - Pe) / scale[7]) ** 2)) < 2e-2
