@@ -1,7 +1,8 @@
 """Throughput benchmark of the fused non-ideal LBM step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload tgv256|tgv256-fp64|tgv256-fp16dev|riemann|shockdrop2d]
+                    [--workload tgv256|tgv256-fp64|tgv256-fp16dev|riemann|shockdrop2d|batched|
+                                shocktube3d|shocktube3d-mlp]
 
 Prints one JSON line (rank 0).  A step is one full time step of the method
 (stream, moments, EOS, correction terms, collide, boundary fill) over the
@@ -39,7 +40,14 @@ WORKLOADS = {
                     "D2Q9 shock-drop 4096x2048 (Ma 1.47 inflow), FP32"),
     "batched": ("batch", dict(), "fp32",
                 "256 uneven D2Q9 shock tubes (128x64 .. 1024x512, Ma 1.1-1.3), one persistent launch per step, FP32"),
+    "shocktube3d-mlp": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
+                        "D3Q27 shock tube 512x256x256 (Ma 1.15), learned closure (2-64-64-3 BF16 MLP), FP32"),
+    "shocktube3d": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
+                    "D3Q27 shock tube 512x256x256 (Ma 1.15), exact closure, FP32"),
 }
+# workloads whose step uses the learned closure, trained before the timed region
+MLP_WORKLOADS = {"shocktube3d-mlp"}
+MLP_TRAIN = dict(snapshots=50, every=20, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5, net_seed=11)
 BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # Longest run from the initial state that stays finite, per (builder, precision):
 # the Ma 0.5 Taylor-Green vortex at 256^3 develops a blow-up after ~250 steps in
@@ -162,6 +170,9 @@ def _oracle_sample(workload, seconds, steps=None, warmup=1):
     elif builder == "batch":
         case = inputs.batch(1)[0]
         sample = "D2Q9 shock tube %dx%d (instance 0 of the batch), FP64 oracle" % case.shape
+    elif builder == "shock_tube_3d":
+        case = inputs.shock_tube_3d(shape=(128, 8, 8), Ma=kw["Ma"], seed=kw["seed"])
+        sample = "D3Q27 shock tube 128x8x8 down-scale, exact closure, FP64 oracle"
     else:
         case = inputs.shock_drop(2, (512, 256), radius=16, center=(128, 128), shock_x=64)
         sample = "D2Q9 shock-drop 512x256 down-scale, FP64 oracle"
@@ -280,6 +291,24 @@ def run_ours(args):
     u = torch.from_numpy(np.ascontiguousarray(np.stack(case.u), dtype=np.float64)).to(dev)
     T = torch.from_numpy(np.ascontiguousarray(case.T, dtype=np.float64)).to(dev)
     P.lbm_init_device(solver.h, rho, u, T)
+    closure_info, net = None, None
+    if args.workload in MLP_WORKLOADS:
+        # same case with the exact closure first: tuned, then timed like the main loop
+        net, closure_info = train_closure(P, dev, case)
+        if not args.no_autotune:
+            P.lbm_autotune(solver.h, 3)
+        P.lbm_step(solver.h, args.warmup)
+        ne = min(args.steps, 100)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        P.lbm_step_async(solver.h, ne)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        P.lbm_sync(solver.h)
+        closure_info["exact_closure_ms_per_step"] = e0.elapsed_time(e1) / ne
+        P.lbm_init_device(solver.h, rho, u, T)
+        net.attach(solver)
     tile = None
     if sk == P.LBM_STEP_FUSED and not args.no_autotune:
         tile = P.lbm_autotune(solver.h, 3)
@@ -344,6 +373,8 @@ def run_ours(args):
             torch.empty_like(h_T).pin_memory()
         tot = np.empty(case.D + 2)
         s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
+        if net is not None:
+            net.attach(s2)
         lib = P.load()
         import ctypes
         vp = lambda t: ctypes.c_void_p(t.data_ptr())
@@ -387,12 +418,40 @@ def run_ours(args):
                          "algorithmic_bytes_per_step": alg_bytes, "peak_source": peak_kind},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "status_flags": flags,
         }
+        if closure_info is not None:
+            em = closure_info["exact_closure_ms_per_step"]
+            closure_info["exact_closure_mlups"] = N / (em * 1e-3) / 1e6
+            closure_info["gain_vs_exact"] = value / world / closure_info["exact_closure_mlups"]
+            line["closure"] = closure_info
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_oracle_leg(args.workload)
         print(json.dumps(line))
+    if net is not None:
+        net.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def train_closure(P, dev, case):
+    """Train the learned closure on solver states (GPU), untimed; returns (net, info)."""
+    import numpy as np
+    import torch
+    import inputs
+    t0 = time.perf_counter()
+    sc = inputs.scenario("shock_drop_d3q27")
+    net = P.Closure(sc["eos"]["a"], sc["eos"]["b"], sc["eos"]["R"], sc["cv"], seed=MLP_TRAIN["net_seed"])
+    rho, e = net.collect_runs(inputs.closure_training_runs(), MLP_TRAIN["snapshots"], MLP_TRAIN["every"],
+                              precision="fp32")
+    net.fit_scaling(rho, e)
+    losses = net.train(rho, e, batch=MLP_TRAIN["batch"], steps=MLP_TRAIN["steps"], lr0=MLP_TRAIN["lr0"],
+                       lr1=MLP_TRAIN["lr1"], seed=MLP_TRAIN["seed"])
+    torch.cuda.synchronize(dev)
+    info = {"kind": "mlp 2-64-64-3, bf16 weights, fp32 accumulate, range-gated exact fallback",
+            "train_samples": int(rho.numel()), "train_steps": MLP_TRAIN["steps"], "batch": MLP_TRAIN["batch"],
+            "final_loss": float(np.mean(losses[-100:])), "train_and_collect_s": time.perf_counter() - t0}
+    del rho, e
+    return net, info
 
 
 def main():
