@@ -309,9 +309,10 @@ def run_ours(args):
         closure_info["exact_closure_ms_per_step"] = e0.elapsed_time(e1) / ne
         P.lbm_init_device(solver.h, rho, u, T)
         net.attach(solver)
-    tile = None
+    tile, tile_ms = None, None
     if sk == P.LBM_STEP_FUSED and not args.no_autotune:
         tile = P.lbm_autotune(solver.h, 3)
+        tile_ms = P.lbm_autotune_times(solver.h)
 
     # warm-up
     builder = WORKLOADS[args.workload][0]
@@ -409,7 +410,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
             "config": {"workload": desc, "nodes": N, "lattice": "D%dQ%d" % (case.D, Q), "precision": prec,
                        "parallelism": "replicas" if world > 1 else "single-gpu",
-                       "tile_shape": tile[0] if tile else None,
+                       "tile_shape": tile[0] if tile else None, "tile_candidates_ms": tile_ms,
                        "timed_chunk_steps": min(chunk, args.steps),
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -197,6 +197,13 @@ int lbm_set_step_kernel(lbm_t h, int kind);
  * Synchronises.  Errors: LBM_EINVAL, LBM_ESTATE (before lbm_init), LBM_ECUDA. */
 int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step);
 
+/* Times of every tile candidate measured by the last lbm_autotune on `h`
+ * (ms per step, in candidate order; the chosen one is the smallest).
+ * Copies min(count, n) values to ms_per_step (host, may be NULL) and
+ * returns the candidate count (0 before any autotune), or LBM_EINVAL for
+ * a NULL handle. */
+int lbm_autotune_times(lbm_t h, float* ms_per_step, int n);
+
 /* Kernel launches enqueued by this handle since creation (for accounting). */
 long long lbm_launch_count(lbm_t h);
 

@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
 EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
-           "lbm_set_step_kernel", "lbm_autotune", "lbm_launch_count", "lbm_destroy", "lbm_last_error", "lbm_version",
+           "lbm_set_step_kernel", "lbm_autotune", "lbm_autotune_times", "lbm_launch_count", "lbm_destroy",
+           "lbm_last_error", "lbm_version",
            "lbm_totals_noalloc", "lbm_totals_noalloc_error",
            "lbm_batch_create", "lbm_batch_set_boundary", "lbm_batch_set_stream", "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_moments", "lbm_batch_flags",
@@ -88,6 +89,7 @@ def load():
         "lbm_set_populations": (I, [P, P, S]),
         "lbm_set_step_kernel": (I, [P, I]),
         "lbm_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]),
+        "lbm_autotune_times": (I, [P, P, I]),
         "lbm_launch_count": (ctypes.c_longlong, [P]),
         "lbm_destroy": (I, [P]),
         "lbm_last_error": (ctypes.c_char_p, []),
@@ -249,6 +251,15 @@ def lbm_autotune(h, reps=3):
     c, ms = ctypes.c_int(), ctypes.c_float()
     _check(load().lbm_autotune(h, reps, ctypes.byref(c), ctypes.byref(ms)))
     return c.value, ms.value
+
+
+def lbm_autotune_times(h):
+    """ms per step of every tile candidate at the last lbm_autotune."""
+    ms = np.zeros(8, dtype=np.float32)
+    n = load().lbm_autotune_times(h, ms.ctypes.data_as(ctypes.c_void_p), 8)
+    if n < 0:
+        _check(n)
+    return ms[:n].tolist()
 
 
 def lbm_launch_count(h):

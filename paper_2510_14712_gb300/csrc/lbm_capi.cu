@@ -425,6 +425,13 @@ int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step) {
   return LBM_OK;
 }
 
+int lbm_autotune_times(lbm_t h, float* ms_per_step, int n) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  for (int k = 0; k < h->tune_n && k < n; ++k)
+    if (ms_per_step) ms_per_step[k] = h->tune_ms[k];
+  return h->tune_n;
+}
+
 long long lbm_launch_count(lbm_t h) { return h ? h->launches : 0; }
 
 int lbm_destroy(lbm_t h) {

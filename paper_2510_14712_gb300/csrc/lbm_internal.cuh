@@ -67,6 +67,8 @@ struct Handle {
   long long launches;
   int closure;                // LBM_CLOSURE_EXACT | LBM_CLOSURE_MLP
   void* mlp_img;              // device copy of the attached network's inference image
+  float tune_ms[8];           // ms per step of every candidate at the last lbm_autotune
+  int tune_n;
 };
 
 struct Batch;

@@ -156,6 +156,7 @@ template <int D, typename S, typename real> struct OpsImpl {
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
+      if (c < 8) h.tune_ms[c] = ms / (reps > 0 ? reps : 1);
       if (ms < bt) {
         bt = ms;
         best = c;
@@ -164,6 +165,7 @@ template <int D, typename S, typename real> struct OpsImpl {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h.tile_cfg = best;
+    h.tune_n = n < 8 ? n : 8;
     if (best_ms) *best_ms = bt / (reps > 0 ? reps : 1);
     return best;
   }
