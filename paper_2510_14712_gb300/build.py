@@ -30,6 +30,15 @@ def sources():
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".cu"))
 
 
+def extra_flags(src):
+    """FP32-arithmetic kernel sets use the hardware reciprocal-based FP32
+    division (about 2 ulp) instead of the IEEE-rounded one."""
+    name = os.path.basename(src)
+    if name.startswith("k_") and ("_fp32" in name or "_fp16" in name):
+        return ["-prec-div=false"]
+    return []
+
+
 def _stale(srcs):
     if not os.path.exists(LIB):
         return True
@@ -48,7 +57,7 @@ def build(force=False, verbose=False):
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + extra_flags(src) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
