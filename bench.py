@@ -44,9 +44,11 @@ WORKLOADS = {
                         "D3Q27 shock tube 512x256x256 (Ma 1.15), learned closure (2-64-64-3 BF16 MLP), FP32"),
     "shocktube3d": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
                     "D3Q27 shock tube 512x256x256 (Ma 1.15), exact closure, FP32"),
+    "shocktube3d-mlp-small": ("shock_tube_3d", dict(shape=(256, 128, 128), Ma=1.15, seed=21), "fp32",
+                              "D3Q27 shock tube 256x128x128 (Ma 1.15), learned closure, FP32 (profiling case)"),
 }
 # workloads whose step uses the learned closure, trained before the timed region
-MLP_WORKLOADS = {"shocktube3d-mlp"}
+MLP_WORKLOADS = {"shocktube3d-mlp", "shocktube3d-mlp-small"}
 MLP_TRAIN = dict(snapshots=50, every=20, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5, net_seed=11)
 BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # Longest run from the initial state that stays finite, per (builder, precision):
@@ -55,7 +57,7 @@ BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # taken in chunks from the initial state (re-initialised outside the timing).
 MAX_CHUNK = {("tgv", "fp32"): 200, ("tgv", "fp16dev"): 100, ("tgv", "fp64"): 400}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16-storage/f32"}
-KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_fused.cuh", "lbm_capi.cu"]
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_fused.cuh", "lbm_mlp.cuh", "lbm_capi.cu"]
 
 
 def build_case(name):
@@ -65,10 +67,11 @@ def build_case(name):
 
 
 def kernel_hash():
+    """Hash of the sources and build flags of the step kernels (traffic counters
+    in profiles/traffic.json are used only while it matches)."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2510_14712_gb300", "csrc")
-    for f in KERNEL_SOURCES:
-        p = os.path.join(src, f)
+    for p in [os.path.join(src, f) for f in KERNEL_SOURCES] + [os.path.join(ROOT, "paper_2510_14712_gb300", "build.py")]:
         if os.path.exists(p):
             h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
@@ -467,7 +470,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=None,
+                    help="AdamW steps of the learned closure (learned-closure workloads)")
     args = ap.parse_args()
+    if args.train_steps is not None:
+        MLP_TRAIN["steps"] = args.train_steps
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
