@@ -143,6 +143,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, device=None):
+    """The largest value of x over all ranks (x itself on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(nodes, steps, world, seconds):
+    """Whole-job throughput of `world` replicas, each updating `nodes` nodes `steps`
+    times, timed by the slowest rank (weak scaling)."""
+    return nodes * steps * world / seconds / 1e6
+
+
 def cpu_oracle_leg(workload, seconds=15.0, steps=None, warmup=1):
     """Time the FP64 oracle on a bounded sample of the workload (runs in a child process)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -349,13 +366,9 @@ def run_ours(args):
         nchunks += 1
     launches = P.lbm_launch_count(solver.h) - launches0
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = N * args.steps * world / (total_ms * 1e-3) / 1e6
+    value = replica_mlups(N, args.steps, world, total_ms * 1e-3)
 
     # roofline of the step kernel(s): algorithmic 4 Q s bytes per node update
     Q = case.lattice
@@ -395,14 +408,10 @@ def run_ours(args):
                 P._check(lib.lbm_step(s2.h, 1))
             done2 += k
         P._check(lib.lbm_moments(s2.h, vp(o_rho), vp(o_u), vp(o_T), tot.ctypes.data_as(ctypes.c_void_p)))
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dev)
         s2.close()
         fb = N * (case.D + 2) * 8
-        e2e = {"value": N * args.steps * world / el / 1e6, "unit": "MLUPS",
+        e2e = {"value": replica_mlups(N, args.steps, world, el), "unit": "MLUPS",
                "h2d_bytes_per_step": fb * inits / args.steps,
                "d2h_bytes_per_step": 4 + (fb + 8 * (case.D + 2)) / args.steps}
 
