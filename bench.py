@@ -334,6 +334,8 @@ def run_ours(args):
         tile = P.lbm_autotune(solver.h, 3)
         tile_ms = P.lbm_autotune_times(solver.h)
 
+    if args.graphs:
+        P.lbm_set_graphs(solver.h, True)
     # warm-up
     builder = WORKLOADS[args.workload][0]
     chunk = MAX_CHUNK.get((builder, prec), 1 << 30)
@@ -353,15 +355,24 @@ def run_ours(args):
     while done < args.steps:
         k = min(chunk, args.steps - done)
         P.lbm_init_device(solver.h, rho, u, T)             # back to the initial state, not timed
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         torch.cuda.synchronize(dev)
-        ev[0].record(stream)
-        for j in range(k):
-            P.lbm_step_async(solver.h, 1)
-            ev[j + 1].record(stream)
-        torch.cuda.synchronize(dev)
-        P.lbm_sync(solver.h)
-        step_ms += [ev[j].elapsed_time(ev[j + 1]) for j in range(k)]
+        if args.graphs:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.lbm_step_async(solver.h, k)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            P.lbm_sync(solver.h)
+            step_ms += [e0.elapsed_time(e1) / k] * k
+        else:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+            ev[0].record(stream)
+            for j in range(k):
+                P.lbm_step_async(solver.h, 1)
+                ev[j + 1].record(stream)
+            torch.cuda.synchronize(dev)
+            P.lbm_sync(solver.h)
+            step_ms += [ev[j].elapsed_time(ev[j + 1]) for j in range(k)]
         done += k
         nchunks += 1
     launches = P.lbm_launch_count(solver.h) - launches0
@@ -423,7 +434,7 @@ def run_ours(args):
             "config": {"workload": desc, "nodes": N, "lattice": "D%dQ%d" % (case.D, Q), "precision": prec,
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "tile_shape": tile[0] if tile else None, "tile_candidates_ms": tile_ms,
-                       "timed_chunk_steps": min(chunk, args.steps),
+                       "timed_chunk_steps": min(chunk, args.steps), "cuda_graphs": bool(args.graphs),
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -479,6 +490,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--graphs", action="store_true",
+                    help="replay captured CUDA graphs (lbm_set_graphs); each chunk is timed as a whole")
     ap.add_argument("--train-steps", type=int, default=None,
                     help="AdamW steps of the learned closure (learned-closure workloads)")
     args = ap.parse_args()

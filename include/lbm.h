@@ -197,6 +197,16 @@ int lbm_set_step_kernel(lbm_t h, int kind);
  * Synchronises.  Errors: LBM_EINVAL, LBM_ESTATE (before lbm_init), LBM_ECUDA. */
 int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step);
 
+/* Graph replay (on = 1) or plain launches (on = 0, the default) for
+ * lbm_step / lbm_step_async with n >= 2: two consecutive steps are captured
+ * once per buffer parity into CUDA graphs and replayed n/2 times (an odd
+ * last step is launched plainly).  The graphs are re-captured automatically
+ * after any change of boundary, closure, tile, step kernel or stream.  With
+ * the legacy default stream the library replays on a stream of its own
+ * (ordered with the legacy stream).  Same results as plain launches.
+ * Errors: LBM_EINVAL (NULL handle), LBM_ECUDA. */
+int lbm_set_graphs(lbm_t h, int on);
+
 /* Times of every tile candidate measured by the last lbm_autotune on `h`
  * (ms per step, in candidate order; the chosen one is the smallest).
  * Copies min(count, n) values to ms_per_step (host, may be NULL) and

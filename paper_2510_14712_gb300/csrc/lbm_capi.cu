@@ -83,6 +83,35 @@ size_t scratch_for(const Handle& h) {
 
 Model<double> host_model(const Handle& h) { return model_of<double>(h.p); }
 
+// Two-step CUDA graphs of a handle, one per starting buffer parity, with the
+// configuration they were captured for (kernel arguments are baked in).
+struct StepGraphs {
+  cudaGraphExec_t exec[2];
+  cudaStream_t stream;        // capture / replay stream (owned when the handle uses the legacy stream)
+  bool own_stream;
+  Params p;
+  void* pop[2];
+  int tile_cfg, closure, step_kernel;
+  long long launches;         // kernel launches per replay
+  bool ready;
+};
+
+void drop_graphs(Handle& h) {
+  StepGraphs* g = static_cast<StepGraphs*>(h.graphs);
+  if (!g) return;
+  for (int k = 0; k < 2; ++k)
+    if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  h.graphs = nullptr;
+}
+
+bool graphs_match(const Handle& h, const StepGraphs& g) {
+  return g.ready && std::memcmp(&g.p, &h.p, sizeof(Params)) == 0 && g.pop[0] == h.pop[0] && g.pop[1] == h.pop[1] &&
+         g.tile_cfg == h.tile_cfg && g.closure == h.closure && g.step_kernel == h.step_kernel &&
+         (g.own_stream ? h.stream == nullptr : g.stream == h.stream);
+}
+
 void free_state(Handle& h) {
   for (int k = 0; k < 2; ++k) {
     if (h.pop[k]) cudaFree(h.pop[k]);
@@ -329,6 +358,55 @@ int lbm_step_async(lbm_t h, int n) {
   const Ops* o = ops_for(*h);
   auto fn = h->step_kernel == LBM_STEP_MULTIPASS ? o->step_multipass : o->step;
   if (!fn) return fail(LBM_EINVAL, "the learned closure runs in the fused step only");
+  if (h->use_graphs && n >= 2) {
+    StepGraphs* g = static_cast<StepGraphs*>(h->graphs);
+    if (!g || !graphs_match(*h, *g)) {
+      drop_graphs(*h);
+      g = new (std::nothrow) StepGraphs();
+      if (!g) return fail(LBM_ENOMEM, "host allocation failed");
+      std::memset(g, 0, sizeof(*g));
+      h->graphs = g;
+      if (h->stream) {
+        g->stream = h->stream;
+      } else {
+        CK(cudaStreamCreate(&g->stream));
+        g->own_stream = true;
+      }
+      const cudaStream_t saved = h->stream;
+      const long long l0 = h->launches;
+      for (int par = 0; par < 2; ++par) {
+        cudaGraph_t graph = nullptr;
+        h->stream = g->stream;
+        cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          fn(*h, h->pop[par], h->pop[par ^ 1]);
+          fn(*h, h->pop[par ^ 1], h->pop[par]);
+          e = cudaStreamEndCapture(g->stream, &graph);
+        }
+        h->stream = saved;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec[par], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          drop_graphs(*h);
+          h->launches = l0;
+          return cuda_fail(e, "step graph capture");
+        }
+      }
+      g->launches = (h->launches - l0) / 2;
+      h->launches = l0;
+      g->p = h->p;
+      g->pop[0] = h->pop[0];
+      g->pop[1] = h->pop[1];
+      g->tile_cfg = h->tile_cfg;
+      g->closure = h->closure;
+      g->step_kernel = h->step_kernel;
+      g->ready = true;
+    }
+    for (; n >= 2; n -= 2) {                 // two steps return to the same parity
+      CK(cudaGraphLaunch(g->exec[h->cur], g->stream));
+      h->launches += g->launches;
+    }
+  }
   for (int k = 0; k < n; ++k) {
     fn(*h, h->pop[h->cur], h->pop[h->cur ^ 1]);
     h->cur ^= 1;
@@ -425,6 +503,16 @@ int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step) {
   return LBM_OK;
 }
 
+int lbm_set_graphs(lbm_t h, int on) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  h->use_graphs = on ? 1 : 0;
+  if (!on) {
+    if (h->graphs) CK(cudaDeviceSynchronize());
+    drop_graphs(*h);
+  }
+  return LBM_OK;
+}
+
 int lbm_autotune_times(lbm_t h, float* ms_per_step, int n) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   for (int k = 0; k < h->tune_n && k < n; ++k)
@@ -436,6 +524,8 @@ long long lbm_launch_count(lbm_t h) { return h ? h->launches : 0; }
 
 int lbm_destroy(lbm_t h) {
   if (!h) return LBM_OK;
+  if (h->graphs) cudaDeviceSynchronize();
+  drop_graphs(*h);
   free_state(*h);
   if (h->mlp_img) cudaFree(h->mlp_img);
   if (h->partials) cudaFree(h->partials);

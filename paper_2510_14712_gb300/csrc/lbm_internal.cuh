@@ -69,6 +69,8 @@ struct Handle {
   void* mlp_img;              // device copy of the attached network's inference image
   float tune_ms[8];           // ms per step of every candidate at the last lbm_autotune
   int tune_n;
+  int use_graphs;             // lbm_set_graphs: replay captured two-step graphs
+  void* graphs;               // StepGraphs (lbm_capi.cu), created on first use
 };
 
 struct Batch;

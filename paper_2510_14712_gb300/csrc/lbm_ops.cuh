@@ -113,10 +113,12 @@ template <int D, typename S, typename real> struct OpsImpl {
         return 3;
       }
     } else {
+      // narrow tiles spread small domains (few columns) over more SMs
       static const LaunchFn c[] = {&Fused<256, 1, 2, CL>::launch, &Fused<128, 1, 4, CL>::launch,
-                                   &Fused<512, 1, 1, CL>::launch};
+                                   &Fused<512, 1, 1, CL>::launch, &Fused<64, 1, 8, CL>::launch,
+                                   &Fused<32, 1, 16, CL>::launch};
       *fns = c;
-      return 3;
+      return 5;
     }
   }
 

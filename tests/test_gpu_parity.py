@@ -339,3 +339,27 @@ def test_full_size_tgv_256_sampled_fp32():
         s.close()
     assert abs(t1[0] / t0[0] - 1) < 1e-6
     assert np.abs(t1[1:4] - t0[1:4]).max() < 1e-6 * t0[0]
+
+
+@pytest.mark.parametrize("case_name,precision,steps", [("riemann", "fp64", 101), ("tgv", "fp32", 40)])
+def test_graph_replay_bit_identical(case_name, precision, steps):
+    """lbm_set_graphs: two-step graph replays give bitwise the same state as plain launches."""
+    import paper_2510_14712_gb300 as P
+    case = inputs.riemann(Nx=200, Ny=3, split=100) if case_name == "riemann" else inputs.tgv(shape=(24, 16, 12))
+    outs = []
+    for graphs in (False, True):
+        s = P.Solver(case, precision=precision).init()
+        P.lbm_set_graphs(s.h, graphs)
+        l0 = P.lbm_launch_count(s.h)
+        s.step(steps)
+        outs.append((s.fields(), P.lbm_launch_count(s.h) - l0))
+        if graphs:
+            # a boundary change re-captures the graphs
+            if case_name == "riemann":
+                P.lbm_set_boundary(s.h, P.LBM_FACE_XHI, P.LBM_BC_OUTFLOW)
+            s.step(4)
+        s.close()
+    (a, la), (b, lb) = outs
+    for k in ("rho", "u", "T"):
+        assert np.array_equal(a[k], b[k]), k
+    assert la == lb
