@@ -244,3 +244,23 @@ def test_learned_closure_shock_tube_d3q27(P, trained):
     used = net.predict(r, e).cpu().numpy()[:, 3]
     assert used.mean() > 0.95, used.mean()
     assert np.isfinite(u2).all()
+
+
+def test_mlp_argument_errors(P):
+    net = make_net(P)
+    r = torch.ones(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.LbmError):
+        net.predict(r, r)                                # no scaling yet
+    with pytest.raises(P.LbmError):
+        net.scaling = np.array([0.4, 0.0, 0.8, 0.05, 0.1, 0.02, 0.5, 0.2, 0.4, 0.1])   # zero half-width
+    net.scaling = np.array([0.4, 0.1, 0.8, 0.05, 0.1, 0.02, 0.5, 0.2, 0.4, 0.1])
+    with pytest.raises(P.LbmError):
+        net.train(r, r, batch=16, steps=1)               # batch below 32
+    with pytest.raises(P.LbmError):
+        net.params = np.full(mlp.NPARAM, np.nan, dtype=np.float32)
+    e0 = torch.empty(0, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.LbmError):
+        net.predict(e0, e0)                              # empty input
+    out = net.predict(r, r)
+    assert out.shape == (4, 4)
+    net.close()

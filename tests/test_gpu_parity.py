@@ -363,3 +363,25 @@ def test_graph_replay_bit_identical(case_name, precision, steps):
     for k in ("rho", "u", "T"):
         assert np.array_equal(a[k], b[k]), k
     assert la == lb
+
+
+def test_domain_beyond_32bit_offsets_rejected():
+    """2Q x plane must stay below 2^32 elements (32-bit offsets in the fused kernel)."""
+    import paper_2510_14712_gb300 as P
+    c = inputs.tgv(shape=(8, 8, 8))
+    with pytest.raises(P.LbmError) as ex:
+        P.lbm_create(27, 448, 448, 448, c.eos, c.tau, c.Pr, c.cv, "fp32")
+    assert ex.value.code == P.LBM_EINVAL
+    # the largest cube below the limit is accepted (and freed again)
+    h = P.lbm_create(27, 416, 416, 416, c.eos, c.tau, c.Pr, c.cv, "fp16dev")
+    P.lbm_destroy(h)
+
+
+def test_single_node_columns_and_ragged_tiles_fp64():
+    """Sizes that leave ragged tiles in x and y and a short z (5 planes) match the oracle."""
+    c = inputs.add_noise(inputs.tgv(shape=(33, 9, 5)), 3)
+    sc = inputs.scenario("tgv_d3q27")
+    c.tau = sc["tau"] * 0.05 / sc["nu"]
+    ref = oracle_run(c, 12)
+    got = gpu_run(c, 12, "fp64")
+    assert_parity(got, ref, 1e-12, "ragged tgv fp64")
