@@ -38,12 +38,16 @@ template <int D, int TX, int TY, int EX = 0> struct FusedGeom {
   static constexpr int BX2 = TX + 4, BY2 = TY + 2 * HY2, N2 = BX2 * BY2;
   static constexpr int BX1 = TX + 2, BY1 = TY + 2 * HY1, N1 = BX1 * BY1;
   static constexpr int NMOM = D + 1;                 // j_0..j_{D-1}, S
-  static constexpr int NPRIM = 3 * D + 4 + EX;       // rho, u[D], T, h, Lam[D], F[D] (, P, c_s^2)
-  static constexpr int P_RHO = 0, P_U = 1, P_T = 1 + D, P_H = 2 + D, P_LAM = 3 + D, P_F = 3 + 2 * D;
-  static constexpr int P_P = 3 + 3 * D, P_CS2 = 4 + 3 * D;
+  // primitive ring on R1 (read at the node and its neighbours): u[D], T, h, Lam[D]
+  static constexpr int NPRIM = 2 * D + 2;
+  static constexpr int P_U = 0, P_T = D, P_H = D + 1, P_LAM = D + 2;
+  // centre ring on the tile only (read at the node): rho, F[D] (, P, c_s^2), two planes
+  static constexpr int NCEN = 1 + D + EX;
+  static constexpr int C_RHO = 0, C_F = 1, C_P = 1 + D, C_CS2 = 2 + D;
   // bytes of the four rings, rounded up to 16 (a closure's table follows them)
   template <typename real> static constexpr size_t smem_bytes() {
-    return (sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1) + 15) & ~size_t(15);
+    return (sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1 + 2 * NCEN * NT) + 15) &
+           ~size_t(15);
   }
 };
 
@@ -120,6 +124,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   real* s_mom = s_rho + 3 * G::N3;                            // [3][NMOM][N1]
   real* s_lap = s_mom + 3 * G::NMOM * G::N1;                  // [3][N2]
   real* s_prm = s_lap + 3 * G::N2;                            // [3][NPRIM][N1]
+  real* s_cen = s_prm + 3 * G::NPRIM * G::N1;                 // [2][NCEN][NT]
 
   const Model<real> m = model_of<real>(p);
   const int tid = threadIdx.x;
@@ -259,18 +264,22 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
         if (act) {
           const real theta = P / rho;
           real* pr = s_prm + (sc * G::NPRIM) * G::N1 + k;
-          pr[G::P_RHO * G::N1] = rho;
           pr[G::P_T * G::N1] = T;
           pr[G::P_H * G::N1] = e + theta;                                                      // Eq. enthalpy
-          if constexpr (CL::kExtra > 0) {
-            pr[G::P_P * G::N1] = P;
-            pr[G::P_CS2 * G::N1] = cs2;
-          }
 #pragma unroll
           for (int a = 0; a < D; ++a) {
             pr[(G::P_U + a) * G::N1] = u[a];
             pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
-            pr[(G::P_F + a) * G::N1] = F[a];
+          }
+          if (lx >= 1 && lx <= TX && ly >= G::HY1 && ly < G::HY1 + TY) {                       // a tile node
+            real* ce = s_cen + ((q & 1) * G::NCEN) * G::NT + (ly - G::HY1) * TX + (lx - 1);
+            ce[G::C_RHO * G::NT] = rho;
+#pragma unroll
+            for (int a = 0; a < D; ++a) ce[(G::C_F + a) * G::NT] = F[a];
+            if constexpr (CL::kExtra > 0) {
+              ce[G::C_P * G::NT] = P;
+              ce[G::C_CS2 * G::NT] = cs2;
+            }
           }
         }
       }
@@ -299,11 +308,12 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
         const real* pm = s_prm + (sm * G::NPRIM) * G::N1;
         const real* pp = s_prm + (sp * G::NPRIM) * G::N1;
         NodeState<D, real> s;
-        s.rho = pc[G::P_RHO * G::N1 + k1];
+        const real* cc = s_cen + ((q & 1) * G::NCEN) * G::NT + tid;
+        s.rho = cc[G::C_RHO * G::NT];
         s.T = pc[G::P_T * G::N1 + k1];
         if constexpr (CL::kExtra > 0) {
-          s.P = pc[G::P_P * G::N1 + k1];
-          s.cs2 = pc[G::P_CS2 * G::N1 + k1];
+          s.P = cc[G::C_P * G::NT];
+          s.cs2 = cc[G::C_CS2 * G::NT];
           s.e = pc[G::P_H * G::N1 + k1] - s.P / s.rho;
         } else {
           s.P = vdw_pressure(m, s.rho, s.T);
@@ -314,7 +324,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           s.u[a] = pc[(G::P_U + a) * G::N1 + k1];
-          s.F[a] = pc[(G::P_F + a) * G::N1 + k1];
+          s.F[a] = cc[(G::C_F + a) * G::NT];
         }
         // neighbour accessors along axis a: (plane pointer, index) of -1 / +1
 #pragma unroll
