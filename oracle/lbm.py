@@ -190,6 +190,70 @@ def galilean_correction(m, rho, u, theta):
     return Phi
 
 
+# ---------------------------------------------------------------------------
+# Shock-capturing numerical transport coefficients (Sec. 4.4, Eqs. shock_cap,
+# shock_cap_k), on interior fields.  Readings: r = 5, so the derivative in
+# |grad^(r-1) .| is the fourth; it is the Euclidean norm of the per-axis
+# five-point fourth differences; delta x^(r+1) = 1 in lattice units; the
+# Gaussian filter is the separable binomial (1, 4, 6, 4, 1)/16 per axis (the
+# paper gives no width); neighbours wrap on periodic axes and are clamped to
+# the nearest interior node on non-periodic x faces.
+# ---------------------------------------------------------------------------
+def _shift(f, a, s, D, periodic):
+    """Interior field f at x + s e_a (wrapped, or clamped on a non-periodic axis)."""
+    ax = D - 1 - a
+    if periodic:
+        return np.roll(f, -s, axis=ax)
+    n = f.shape[ax]
+    idx = np.clip(np.arange(n) + s, 0, n - 1)
+    return np.take(f, idx, axis=ax)
+
+
+def strain_rate_magnitude(u, D, per):
+    """S = |grad u + grad u^T| / 2 (Frobenius norm), central differences."""
+    g = [[0.5 * (_shift(u[b], a, 1, D, per[a]) - _shift(u[b], a, -1, D, per[a])) for b in range(D)]
+         for a in range(D)]
+    return 0.5 * np.sqrt(sum((g[a][b] + g[b][a]) ** 2 for a in range(D) for b in range(D)))
+
+
+def entropy_gradient_magnitude(rho, T, b, R, cv, D, per):
+    """|grad s| with grad s = (c_v/T) grad T - R/(rho (1 - b rho)) grad rho (van der Waals)."""
+    gs = []
+    for a in range(D):
+        gT = 0.5 * (_shift(T, a, 1, D, per[a]) - _shift(T, a, -1, D, per[a]))
+        gr = 0.5 * (_shift(rho, a, 1, D, per[a]) - _shift(rho, a, -1, D, per[a]))
+        gs.append(cv / T * gT - R / (rho * (1.0 - b * rho)) * gr)
+    return np.sqrt(sum(x * x for x in gs))
+
+
+def fourth_difference_norm(f, D, per):
+    """sqrt(sum_a (d_a^4 f)^2), d_a^4 the five-point fourth difference (1, -4, 6, -4, 1)."""
+    acc = 0.0
+    for a in range(D):
+        d4 = (_shift(f, a, 2, D, per[a]) - 4.0 * _shift(f, a, 1, D, per[a]) + 6.0 * f
+              - 4.0 * _shift(f, a, -1, D, per[a]) + _shift(f, a, -2, D, per[a]))
+        acc = acc + d4 * d4
+    return np.sqrt(acc)
+
+
+def binomial_filter(f, D, per):
+    """Separable (1, 4, 6, 4, 1)/16 filter along every axis."""
+    for a in range(D):
+        f = (_shift(f, a, -2, D, per[a]) + 4.0 * _shift(f, a, -1, D, per[a]) + 6.0 * f
+             + 4.0 * _shift(f, a, 1, D, per[a]) + _shift(f, a, 2, D, per[a])) / 16.0
+    return f
+
+
+def numerical_transport(rho, u, T, cs2, coef, b, R, cv, D, per):
+    """(mu, eta, k)^num = (rho C_mu F4(S), rho C_eta F4(S), rho c_s C_k F4(|grad s|)),
+    F4 = filtered fourth-difference norm; c_s = sqrt(max(c_s^2, 0))."""
+    C_mu, C_eta, C_k = coef
+    s4 = binomial_filter(fourth_difference_norm(strain_rate_magnitude(u, D, per), D, per), D, per)
+    g4 = binomial_filter(fourth_difference_norm(entropy_gradient_magnitude(rho, T, b, R, cv, D, per), D, per),
+                         D, per)
+    return rho * C_mu * s4, rho * C_eta * s4, rho * np.sqrt(np.maximum(cs2, 0.0)) * C_k * g4
+
+
 class Model:
     """Constants of one run: lattice, vdW parameters, transport and boundaries.
 
@@ -216,6 +280,10 @@ class Model:
         # for Eqs. lbm_temp, Pvdw and vdW_speed_of_sound (a learned closure);
         # None: the exact van der Waals relations.
         self.closure = None
+        # Optional shock capturing (C_mu, C_eta, C_k) of Sec. 4.4: numerical
+        # transport coefficients added to mu, eta, k; those of step t come from
+        # the primitive fields of step t-1 (zero at the first step).  None: off.
+        self.shock_capturing = None
         self.periodic_x = (x_low == "periodic")
         if (x_high == "periodic") != self.periodic_x:
             raise ValueError("x is periodic on both faces or on neither")
@@ -261,6 +329,7 @@ class Sim:
         rho, u, T = self._extend(rho, u, T)
         self.f, self.g = m.state_eq(rho, u, T)
         self.t = 0
+        self.visc = None           # numerical (mu, eta, k) on the interior for the next collision
 
     def _extend(self, rho, u, T):
         """Extend the initial primitive fields into the x ghost layers."""
@@ -324,8 +393,26 @@ class Sim:
         else:
             e, cs2 = q["e"], q["cs2"]
         h = e + P / rho                                                # Eq. enthalpy
-        alpha = bulk_shift(D, rho, cs2, P, m.eta_over_mu)              # Eq. corr_bulk
-        tau = m.mu / P                                                 # tau = mu / P
+        if m.shock_capturing is None:
+            alpha = bulk_shift(D, rho, cs2, P, m.eta_over_mu)          # Eq. corr_bulk
+            tau = m.mu / P                                             # tau = mu / P
+            k_over_mu = m.k_over_mu
+        else:
+            # effective coefficients {mu, eta, k} + {mu, eta, k}^num (Sec. 4.4)
+            I = m.interior()
+            num = [np.zeros_like(rho) for _ in range(3)]
+            if self.visc is not None:
+                for k in range(3):
+                    num[k][I] = self.visc[k]
+            mu_e = m.mu + num[0]
+            eta_e = m.eta_over_mu * m.mu + num[1]
+            k_e = m.k_over_mu * m.mu + num[2]
+            alpha = bulk_shift(D, rho, cs2, P, eta_e / mu_e)           # Eq. corr_bulk
+            tau = mu_e / P
+            k_over_mu = k_e / mu_e
+            per = [m.periodic_x] + [True] * (D - 1)
+            self.visc = numerical_transport(rho[I], [ua[I] for ua in u], T[I], cs2[I], m.shock_capturing,
+                                            m.b, m.R, m.cv, D, per)
         beta = 1.0 / (2.0 * tau + 1.0)                                 # Eq. beta_main
 
         # step 4: derivatives (central; upwind for Phi)
@@ -343,7 +430,7 @@ class Sim:
         else:
             # Eq. sh_T_1 in energy form (e linear in T at fixed rho): e* = e - |F|^2/(2 rho^2)
             e_s = e - 0.5 * sum(F[a] * F[a] for a in range(D)) / (rho * rho)
-        qc = heat_flux_correction(P, gradh, gradT, m.k_over_mu)        # Eq. qc_1
+        qc = heat_flux_correction(P, gradh, gradT, k_over_mu)          # Eq. qc_1
 
         # step 6: attractors
         feq = f_equilibrium(rho, u, [theta + u[a] * u[a] for a in range(D)], c)          # Eq. LBMeq

@@ -120,7 +120,7 @@ def acoustic_decay(L=64, nu=0.02, eta=1.0, Max=0.0):
     return sig, theory
 
 
-def shock_tube(Ma=1.2, Nx=400, steps=(100, 250)):
+def shock_tube(Ma=1.2, Nx=400, steps=(100, 250), shock_capturing=None):
     """Planar shock from the Rankine-Hugoniot post-state into vapour at rest (Sec. 4.4 states).
 
     Returns (speed measured, speed RH, plateau (rho, u, T) measured, RH post-state).
@@ -132,6 +132,7 @@ def shock_tube(Ma=1.2, Nx=400, steps=(100, 250)):
                                              eos["a"], eos["b"], eos["R"], sc["cv"])
     m = lbm.Model(2, (Nx, 1), eos, sc["tau"], sc["Pr"], sc["cv"],
                   x_low=("inflow", (r2, [u2, 0.0], T2)), x_high="outflow")
+    m.shock_capturing = shock_capturing
     x = np.arange(Nx)[None, :]
     behind = x < 50
     rho = np.where(behind, r2, vap["rho"])
