@@ -411,7 +411,9 @@ class Sim:
             tau = mu_e / P
             k_over_mu = k_e / mu_e
             per = [m.periodic_x] + [True] * (D - 1)
-            self.visc = numerical_transport(rho[I], [ua[I] for ua in u], T[I], cs2[I], m.shock_capturing,
+            # c_s of k^num: the van der Waals sound speed at (rho, T), whatever the closure
+            cs2_vdw = thermo.sound_speed_sq(rho[I], T[I], m.a, m.b, m.R, m.cv)
+            self.visc = numerical_transport(rho[I], [ua[I] for ua in u], T[I], cs2_vdw, m.shock_capturing,
                                             m.b, m.R, m.cv, D, per)
         beta = 1.0 / (2.0 * tau + 1.0)                                 # Eq. beta_main
 
