@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
 EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
-           "lbm_set_step_kernel", "lbm_autotune", "lbm_autotune_times", "lbm_set_graphs", "lbm_launch_count",
+           "lbm_set_step_kernel", "lbm_autotune", "lbm_autotune_times", "lbm_set_graphs",
+           "lbm_set_shock_capturing", "lbm_launch_count",
            "lbm_destroy",
            "lbm_last_error", "lbm_version",
            "lbm_totals_noalloc", "lbm_totals_noalloc_error",
@@ -92,6 +93,7 @@ def load():
         "lbm_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]),
         "lbm_autotune_times": (I, [P, P, I]),
         "lbm_set_graphs": (I, [P, I]),
+        "lbm_set_shock_capturing": (I, [P, D, D, D]),
         "lbm_launch_count": (ctypes.c_longlong, [P]),
         "lbm_destroy": (I, [P]),
         "lbm_last_error": (ctypes.c_char_p, []),
@@ -253,6 +255,10 @@ def lbm_autotune(h, reps=3):
     c, ms = ctypes.c_int(), ctypes.c_float()
     _check(load().lbm_autotune(h, reps, ctypes.byref(c), ctypes.byref(ms)))
     return c.value, ms.value
+
+
+def lbm_set_shock_capturing(h, C_mu=0.1, C_eta=0.0, C_k=0.1):
+    _check(load().lbm_set_shock_capturing(h, C_mu, C_eta, C_k))
 
 
 def lbm_set_graphs(h, on=True):

@@ -123,6 +123,26 @@ void free_state(Handle& h) {
   h.io_dev = nullptr;
 }
 
+// shock-capturing fields: rho, u, T of the last step (D+2 planes), the
+// numerical mu, eta, k (3 planes), work (4 planes), in compute precision
+size_t sc_bytes(const Handle& h) {
+  return size_t(h.D + 9) * size_t(h.p.plane) * (h.precision == LBM_FP64 ? 8 : 4);
+}
+
+int sc_alloc(Handle& h) {
+  if (h.sc_buf) cudaFree(h.sc_buf);
+  h.sc_buf = nullptr;
+  h.p.sc_prims = nullptr;
+  h.p.sc_visc = nullptr;
+  if (!h.p.sc_on) return LBM_OK;
+  CK(cudaMalloc(&h.sc_buf, sc_bytes(h)));
+  CK(cudaMemsetAsync(h.sc_buf, 0, sc_bytes(h), h.stream));
+  const size_t es = h.precision == LBM_FP64 ? 8 : 4;
+  h.p.sc_prims = h.sc_buf;
+  h.p.sc_visc = static_cast<char*>(h.sc_buf) + size_t(h.D + 2) * size_t(h.p.plane) * es;
+  return LBM_OK;
+}
+
 // geometry of the padded layout and the device allocations that depend on it
 int layout(Handle& h) {
   free_state(h);
@@ -144,7 +164,7 @@ int layout(Handle& h) {
   CK(cudaMalloc(&h.io_dev, h.io_bytes));
   h.cur = 0;
   h.initialized = 0;
-  return LBM_OK;
+  return sc_alloc(h);
 }
 
 void set_face_eq(Handle& h, int face) {
@@ -325,6 +345,7 @@ int lbm_set_stream(lbm_t h, void* stream) {
 
 static int init_common(lbm_t h, const double* d_rho, const double* d_u, const double* d_T) {
   CK(cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream));
+  if (h->sc_buf) CK(cudaMemsetAsync(h->sc_buf, 0, sc_bytes(*h), h->stream));   // no numerical transport at step 0
   h->cur = 0;
   h->tile_cfg = tuned_cfg(*h);
   ops_for(*h)->init(*h, d_rho, d_u, d_T);
@@ -503,6 +524,27 @@ int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step) {
   return LBM_OK;
 }
 
+int lbm_set_shock_capturing(lbm_t h, double C_mu, double C_eta, double C_k) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!(C_mu >= 0) || !(C_eta >= 0) || !(C_k >= 0) || !std::isfinite(C_mu) || !std::isfinite(C_eta) ||
+      !std::isfinite(C_k))
+    return fail(LBM_EINVAL, "shock-capturing coefficients must be finite and >= 0");
+  const int on = (C_mu > 0 || C_eta > 0 || C_k > 0) ? 1 : 0;
+  h->p.sc_c[0] = C_mu;
+  h->p.sc_c[1] = C_eta;
+  h->p.sc_c[2] = C_k;
+  if (on != h->p.sc_on) {
+    CK(cudaStreamSynchronize(h->stream));
+    h->p.sc_on = on;
+    int rc = sc_alloc(*h);
+    if (rc != LBM_OK) {
+      h->p.sc_on = 0;
+      return rc;
+    }
+  }
+  return LBM_OK;
+}
+
 int lbm_set_graphs(lbm_t h, int on) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   h->use_graphs = on ? 1 : 0;
@@ -527,6 +569,7 @@ int lbm_destroy(lbm_t h) {
   if (h->graphs) cudaDeviceSynchronize();
   drop_graphs(*h);
   free_state(*h);
+  if (h->sc_buf) cudaFree(h->sc_buf);
   if (h->mlp_img) cudaFree(h->mlp_img);
   if (h->partials) cudaFree(h->partials);
   if (h->totals_dev) cudaFree(h->totals_dev);

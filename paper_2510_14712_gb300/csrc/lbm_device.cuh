@@ -132,6 +132,9 @@ template <int D, typename real> struct NodeFields {
 // e is the specific internal energy.
 template <int D, typename real> struct NodeState {
   real rho, u[D], F[D], T, P, cs2, e;
+  // shock capturing (Sec. 4.4): numerical mu, eta, k added to the constant ones
+  bool sc;
+  real mu_num, eta_num, k_num;
   real div_u;            // central divergence of u
   real gradT[D], gradh[D];
   real dLam[D];          // upwind derivative of Lambda_a along a (Sec. 3.2)
@@ -157,8 +160,15 @@ template <int D, typename real> struct Attractors {
     const real theta = P * inv_rho;                                        // Eq. theta
     e = s.e;
     const real cs2 = s.cs2;
-    const real alpha = real(D + 2) / real(D) - rho * cs2 / P - m.eta_over_mu;   // Eq. corr_bulk
-    const real tau = m.mu / P;                                             // tau = mu / P
+    real eta_over_mu = m.eta_over_mu, mu = m.mu, k_over_mu = m.k_over_mu;
+    if (s.sc) {                                                            // {mu, eta, k} + {..}^num
+      const real mu_e = m.mu + s.mu_num;
+      eta_over_mu = (m.eta_over_mu * m.mu + s.eta_num) / mu_e;
+      k_over_mu = (m.k_over_mu * m.mu + s.k_num) / mu_e;
+      mu = mu_e;
+    }
+    const real alpha = real(D + 2) / real(D) - rho * cs2 / P - eta_over_mu;     // Eq. corr_bulk
+    const real tau = mu / P;                                               // tau = mu / P
     const real beta = real(1) / (real(2) * tau + real(1));                 // Eq. beta_main
     twobeta = real(2) * beta;
     omb = real(1) - beta;
@@ -174,7 +184,7 @@ template <int D, typename real> struct Attractors {
     // e* = e - |F|^2 / (2 rho^2)
     e_s = e - FF * real(0.5) * inv_rho * inv_rho;
 #pragma unroll
-    for (int a = 0; a < D; ++a) qc[a] = P * (s.gradh[a] - m.k_over_mu * s.gradT[a]);
+    for (int a = 0; a < D; ++a) qc[a] = P * (s.gradh[a] - k_over_mu * s.gradT[a]);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const real Phi = -s.dLam[a] * inv_rho;                               // Eq. correction

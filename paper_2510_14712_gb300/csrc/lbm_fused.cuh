@@ -272,6 +272,20 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
             pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
           }
           if (lx >= 1 && lx <= TX && ly >= G::HY1 && ly < G::HY1 + TY) {                       // a tile node
+            if (p.sc_on && q >= mb && q < me) {
+              // this step's rho, u, T for the shock-capturing coefficients of the next step
+              const int tx = x0 + lx - 1, ty = D == 3 ? y0 + ly - G::HY1 : 0;
+              if (tx < p.Nx && (D == 2 || ty < p.Ny)) {
+                const int mq = modp(q, Nm);
+                const long long o = (D == 3 ? ((long long)mq * p.Ny + ty) * p.pitch : (long long)mq * p.pitch) +
+                                    tx + p.G;
+                real* W = static_cast<real*>(p.sc_prims);
+                W[o] = rho;
+#pragma unroll
+                for (int a = 0; a < D; ++a) W[(1 + a) * p.plane + o] = u[a];
+                W[(1 + D) * p.plane + o] = T;
+              }
+            }
             real* ce = s_cen + ((q & 1) * G::NCEN) * G::NT + (ly - G::HY1) * TX + (lx - 1);
             ce[G::C_RHO * G::NT] = rho;
 #pragma unroll
@@ -319,6 +333,15 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           s.P = vdw_pressure(m, s.rho, s.T);
           s.cs2 = vdw_cs2(m, s.rho, s.T);
           s.e = vdw_energy(m, s.rho, s.T);
+        }
+        s.sc = p.sc_on != 0;
+        s.mu_num = s.eta_num = s.k_num = real(0);
+        if (s.sc) {
+          const long long o = (D == 3 ? ((long long)mq * p.Ny + gy) * p.pitch : (long long)mq * p.pitch) + gx + p.G;
+          const real* V = static_cast<const real*>(p.sc_visc);
+          s.mu_num = V[o];
+          s.eta_num = V[p.plane + o];
+          s.k_num = V[2 * p.plane + o];
         }
         s.div_u = 0;
 #pragma unroll

@@ -32,6 +32,14 @@ struct Params {
   float ref[54];
   // learned closure: device inference image (mlp::Image), NULL for the exact closure
   const void* mlp;
+  // shock capturing (Sec. 4.4): on/off, coefficients C_mu, C_eta, C_k; the step
+  // writes rho, u[D], T of every interior node to sc_prims (D+2 planes) and
+  // reads the numerical mu, eta, k of the node from sc_visc (3 planes), both in
+  // compute precision on the padded plane layout
+  int sc_on;
+  double sc_c[3];
+  void* sc_prims;
+  const void* sc_visc;
 };
 
 template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
@@ -71,6 +79,7 @@ struct Handle {
   int tune_n;
   int use_graphs;             // lbm_set_graphs: replay captured two-step graphs
   void* graphs;               // StepGraphs (lbm_capi.cu), created on first use
+  void* sc_buf;               // shock capturing: prims (D+2), visc (3), work (4) planes
 };
 
 struct Batch;

@@ -273,6 +273,14 @@ __global__ void k_collide(Params p, const typename Store<S>::T* A, typename Stor
   s.P = vdw_pressure(m, s.rho, s.T);
   s.cs2 = vdw_cs2(m, s.rho, s.T);
   s.e = vdw_energy(m, s.rho, s.T);
+  s.sc = p.sc_on != 0;
+  s.mu_num = s.eta_num = s.k_num = real(0);
+  if (s.sc) {
+    const real* V = static_cast<const real*>(p.sc_visc);
+    s.mu_num = V[o];
+    s.eta_num = V[p.plane + o];
+    s.k_num = V[2 * p.plane + o];
+  }
   s.div_u = 0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {

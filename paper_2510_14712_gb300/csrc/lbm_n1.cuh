@@ -1,0 +1,155 @@
+// lbm_n1.cuh - shock-capturing numerical transport coefficients (Sec. 4.4,
+// Eqs. shock_cap and shock_cap_k), computed after each step from that step's
+// primitive fields and used by the next step's collision:
+//
+//   {mu, eta}^num = rho C_{mu,eta} F(|grad^4 S|),  k^num = rho c_s C_k F(|grad^4 |grad s||)
+//
+// with S = |grad u + grad u^T| / 2, grad s = (c_v/T) grad T - R/(rho (1 - b rho)) grad rho,
+// |grad^4 f| = sqrt(sum_a (d_a^4 f)^2) over the per-axis five-point fourth
+// differences (r = 5, delta x^(r+1) = 1), F the separable binomial filter
+// (1, 4, 6, 4, 1)/16 along every axis, c_s the van der Waals sound speed
+// at (rho, T).  Neighbours wrap on periodic axes and are clamped to the
+// nearest interior node on non-periodic x faces.  Fields live on the padded
+// plane layout of the handle (offset (z Ny + y) pitch + x + G, one plane per
+// component); one thread per interior node.
+#pragma once
+
+#include "lbm_fused.cuh"
+
+namespace lbm {
+
+// interior neighbour (x, y, z) + s e_a: wrapped, or clamped on a non-periodic x
+__device__ __forceinline__ long long n1_off(const Params& p, int x, int y, int z, int a, int s) {
+  if (a == 0) {
+    x += s;
+    if (p.periodic_x) x = modp(x, p.Nx);
+    else x = x < 0 ? 0 : (x >= p.Nx ? p.Nx - 1 : x);
+  } else if (a == 1) {
+    y = modp(y + s, p.Ny);
+  } else {
+    z = modp(z + s, p.Nz);
+  }
+  return ((long long)z * p.Ny + y) * p.pitch + x + p.G;
+}
+
+__device__ __forceinline__ bool n1_node(const Params& p, int& x, int& y, int& z, long long& o) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)p.Nx * p.Ny * p.Nz;
+  if (gid >= n) return false;
+  x = int(gid % p.Nx);
+  const long long r = gid / p.Nx;
+  y = int(r % p.Ny);
+  z = int(r / p.Ny);
+  o = ((long long)z * p.Ny + y) * p.pitch + x + p.G;
+  return true;
+}
+
+// S and |grad s| of every interior node: out[0 .. plane) = S, out[plane ..) = |grad s|
+template <int D, typename real>
+__global__ void k_n1_strain(Params p, const real* __restrict__ rho, const real* __restrict__ u,
+                            const real* __restrict__ T, real* __restrict__ out) {
+  int x, y, z;
+  long long o;
+  if (!n1_node(p, x, y, z, o)) return;
+  real g[D][D];                                    // g[a][b] = d_a u_b (central)
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const long long op = n1_off(p, x, y, z, a, 1), om = n1_off(p, x, y, z, a, -1);
+#pragma unroll
+    for (int b = 0; b < D; ++b) g[a][b] = real(0.5) * (u[b * p.plane + op] - u[b * p.plane + om]);
+  }
+  real acc = real(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) acc += (g[a][b] + g[b][a]) * (g[a][b] + g[b][a]);
+  out[o] = real(0.5) * sqrt(acc);
+  const real r = rho[o], t = T[o];
+  const real cR = real(p.R) / (r * (real(1) - real(p.b) * r)), cT = real(p.cv) / t;
+  real gs2 = real(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const long long op = n1_off(p, x, y, z, a, 1), om = n1_off(p, x, y, z, a, -1);
+    const real gT = real(0.5) * (T[op] - T[om]), gr = real(0.5) * (rho[op] - rho[om]);
+    const real gs = cT * gT - cR * gr;
+    gs2 += gs * gs;
+  }
+  out[p.plane + o] = sqrt(gs2);
+}
+
+// norm of the per-axis fourth differences of the two fields of `in`
+template <int D, typename real>
+__global__ void k_n1_d4(Params p, const real* __restrict__ in, real* __restrict__ out) {
+  int x, y, z;
+  long long o;
+  if (!n1_node(p, x, y, z, o)) return;
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    const real* v = in + f * p.plane;
+    real acc = real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const real d4 = v[n1_off(p, x, y, z, a, 2)] - real(4) * v[n1_off(p, x, y, z, a, 1)] + real(6) * v[o] -
+                      real(4) * v[n1_off(p, x, y, z, a, -1)] + v[n1_off(p, x, y, z, a, -2)];
+      acc += d4 * d4;
+    }
+    out[f * p.plane + o] = sqrt(acc);
+  }
+}
+
+// binomial (1, 4, 6, 4, 1)/16 along axis a of the two fields of `in`
+template <int D, typename real>
+__global__ void k_n1_filter(Params p, int a, const real* __restrict__ in, real* __restrict__ out) {
+  int x, y, z;
+  long long o;
+  if (!n1_node(p, x, y, z, o)) return;
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    const real* v = in + f * p.plane;
+    out[f * p.plane + o] = (v[n1_off(p, x, y, z, a, -2)] + real(4) * v[n1_off(p, x, y, z, a, -1)] +
+                            real(6) * v[o] + real(4) * v[n1_off(p, x, y, z, a, 1)] +
+                            v[n1_off(p, x, y, z, a, 2)]) / real(16);
+  }
+}
+
+// the coefficients from the filtered norms: visc[0..2] planes = mu, eta, k numerical
+template <int D, typename real>
+__global__ void k_n1_coef(Params p, const real* __restrict__ in, const real* __restrict__ rho,
+                          const real* __restrict__ T, real* __restrict__ visc) {
+  int x, y, z;
+  long long o;
+  if (!n1_node(p, x, y, z, o)) return;
+  const Model<real> m = model_of<real>(p);
+  const real r = rho[o];
+  const real s4 = in[o], g4 = in[p.plane + o];
+  const real cs2 = vdw_cs2(m, r, T[o]);
+  const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
+  visc[o] = r * real(p.sc_c[0]) * s4;
+  visc[p.plane + o] = r * real(p.sc_c[1]) * s4;
+  visc[2 * p.plane + o] = r * cs * real(p.sc_c[2]) * g4;
+}
+
+// the whole update of the coefficients: rho, u (D planes), T -> visc (3 planes),
+// using work (4 planes); D + 3 launches
+template <int D, typename real>
+inline int n1_update(const Params& p, cudaStream_t st, const real* rho, const real* u, const real* T, real* visc,
+                     real* work) {
+  const long long n = (long long)p.Nx * p.Ny * p.Nz;
+  const unsigned grid = unsigned((n + 255) / 256);
+  real* w0 = work;
+  real* w1 = work + 2 * p.plane;
+  k_n1_strain<D, real><<<grid, 256, 0, st>>>(p, rho, u, T, w0);
+  k_n1_d4<D, real><<<grid, 256, 0, st>>>(p, w0, w1);
+  real* src = w1;
+  real* dst = w0;
+  for (int a = 0; a < D; ++a) {
+    k_n1_filter<D, real><<<grid, 256, 0, st>>>(p, a, src, dst);
+    real* t = src;
+    src = dst;
+    dst = t;
+  }
+  k_n1_coef<D, real><<<grid, 256, 0, st>>>(p, src, rho, T, visc);
+  return D + 3;
+}
+
+}  // namespace lbm

@@ -5,7 +5,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "lbm_fused.cuh"
+#include "lbm_n1.cuh"
 
 namespace lbm {
 
@@ -130,11 +130,24 @@ template <int D, typename S, typename real> struct OpsImpl {
     }
   }
 
+  // shock capturing: numerical mu, eta, k for the next step from this step's
+  // rho, u (D planes), T
+  static void shock_capturing(Handle& h, const real* rho, const real* u, const real* T) {
+    const Params& p = h.p;
+    real* visc = static_cast<real*>(const_cast<void*>(p.sc_visc));
+    real* work = visc + 3 * p.plane;
+    h.launches += n1_update<D, real>(p, h.stream, rho, u, T, visc, work);
+  }
+
   template <class CL> static void step_cl(Handle& h, const void* src, void* dst) {
     const LaunchFn* fns;
     const int n = candidates<CL>(&fns);
     fns[h.tile_cfg < n ? h.tile_cfg : 0](h, src, dst);
     ghosts(h, dst);
+    if (h.p.sc_on) {
+      const real* W = static_cast<const real*>(h.p.sc_prims);
+      shock_capturing(h, W, W + h.p.plane, W + (1 + D) * h.p.plane);
+    }
   }
   static void step(Handle& h, const void* src, void* dst) { step_cl<ExactClosure<real>>(h, src, dst); }
 
@@ -183,6 +196,7 @@ template <int D, typename S, typename real> struct OpsImpl {
       k_ghosts<D, S><<<grid_for(2LL * p.G * p.Ny * p.Nz), kBlock, 0, h.stream>>>(p, reinterpret_cast<ST*>(dst));
       h.launches += 1;
     }
+    if (p.sc_on) shock_capturing(h, M(h), W(h), W(h) + D * p.plane);
   }
 
   static void macro(Handle& h, const void* src, double* rho, double* u, double* T, double* totals) {
