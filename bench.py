@@ -44,18 +44,23 @@ WORKLOADS = {
                         "D3Q27 shock tube 512x256x256 (Ma 1.15), learned closure (2-64-64-3 BF16 MLP), FP32"),
     "shocktube3d": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
                     "D3Q27 shock tube 512x256x256 (Ma 1.15), exact closure, FP32"),
+    "strongshock3d": ("strong_shock", dict(D=3, shape=(512, 256, 256), seed=21), "fp32",
+                      "D3Q27 shock tube 512x256x256 at the workloads' Ma 1.47 (U^2 = 16), shock capturing "
+                      "C_mu = C_k = 0.3, FP32"),
     "shocktube3d-mlp-small": ("shock_tube_3d", dict(shape=(256, 128, 128), Ma=1.15, seed=21), "fp32",
                               "D3Q27 shock tube 256x128x128 (Ma 1.15), learned closure, FP32 (profiling case)"),
 }
 # workloads whose step uses the learned closure, trained before the timed region
 MLP_WORKLOADS = {"shocktube3d-mlp", "shocktube3d-mlp-small"}
+# workloads that run with shock capturing (C_mu, C_eta, C_k)
+SC_WORKLOADS = {"strongshock3d": (0.3, 0.0, 0.3)}
 MLP_TRAIN = dict(snapshots=50, every=20, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5, net_seed=11)
 BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # Longest run from the initial state that stays finite, per (builder, precision):
 # the Ma 0.5 Taylor-Green vortex at 256^3 develops a blow-up after ~250 steps in
 # FP32 (~150 in FP16-deviation) without extra dissipation, so timed steps are
 # taken in chunks from the initial state (re-initialised outside the timing).
-MAX_CHUNK = {("tgv", "fp32"): 200, ("tgv", "fp16dev"): 100, ("tgv", "fp64"): 400}
+MAX_CHUNK = {("tgv", "fp32"): 200, ("tgv", "fp16dev"): 100, ("tgv", "fp64"): 400, ("strong_shock", "fp32"): 500}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16-storage/f32"}
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_fused.cuh", "lbm_mlp.cuh", "lbm_capi.cu"]
 
@@ -193,10 +198,14 @@ def _oracle_sample(workload, seconds, steps=None, warmup=1):
     elif builder == "shock_tube_3d":
         case = inputs.shock_tube_3d(shape=(128, 8, 8), Ma=kw["Ma"], seed=kw["seed"])
         sample = "D3Q27 shock tube 128x8x8 down-scale, exact closure, FP64 oracle"
+    elif builder == "strong_shock":
+        case = inputs.strong_shock(3, (128, 8, 8), seed=kw["seed"])
+        sample = "D3Q27 Ma 1.47 shock tube 128x8x8 down-scale with shock capturing, FP64 oracle"
     else:
         case = inputs.shock_drop(2, (512, 256), radius=16, center=(128, 128), shock_x=64)
         sample = "D2Q9 shock-drop 512x256 down-scale, FP64 oracle"
     m = olbm.Model(case.D, case.shape, case.eos, case.tau, case.Pr, case.cv, case.x_low, case.x_high)
+    m.shock_capturing = SC_WORKLOADS.get(workload)
     s = olbm.Sim(m, case.rho, case.u, case.T)
     s.step(warmup)
     done, t0 = 0, time.perf_counter()
@@ -307,6 +316,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     sk = P.LBM_STEP_MULTIPASS if args.step_kernel == "multipass" else P.LBM_STEP_FUSED
     solver = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
+    sc_coef = SC_WORKLOADS.get(args.workload)
+    if sc_coef:
+        P.lbm_set_shock_capturing(solver.h, *sc_coef)
     rho = torch.from_numpy(np.ascontiguousarray(case.rho, dtype=np.float64)).to(dev)
     u = torch.from_numpy(np.ascontiguousarray(np.stack(case.u), dtype=np.float64)).to(dev)
     T = torch.from_numpy(np.ascontiguousarray(case.T, dtype=np.float64)).to(dev)
@@ -401,6 +413,8 @@ def run_ours(args):
             torch.empty_like(h_T).pin_memory()
         tot = np.empty(case.D + 2)
         s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
+        if sc_coef:
+            P.lbm_set_shock_capturing(s2.h, *sc_coef)
         if net is not None:
             net.attach(s2)
         lib = P.load()
@@ -435,6 +449,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "tile_shape": tile[0] if tile else None, "tile_candidates_ms": tile_ms,
                        "timed_chunk_steps": min(chunk, args.steps), "cuda_graphs": bool(args.graphs),
+                       "shock_capturing": list(sc_coef) if sc_coef else None,
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

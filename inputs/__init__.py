@@ -217,6 +217,19 @@ def shock_tube_3d(shape=(768, 32, 32), Ma=1.15, shock_x=None, seed=None, rel=1e-
     return c
 
 
+def strong_shock(D=3, shape=(768, 32, 32), seed=None, rel=1e-3):
+    """Planar Ma 1.47 shock tube (strong_shock_d2q9 / _d3q27: the shock strength
+    of the shock-drop workloads, velocity scale U^2 = 16, no drop), shock at
+    Nx/8, optional seeded perturbation.  Needs shock capturing to stay stable
+    in wide domains."""
+    name = "strong_shock_d2q9" if D == 2 else "strong_shock_d3q27"
+    c = shock_drop(D, shape, shock_x=shape[0] // 8, with_drop=False, sc=scenario(name))
+    c.name = name
+    if seed is not None:
+        add_noise(c, seed, rel)
+    return c
+
+
 def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25):
     """(case, e_scale) runs whose states train the learned closure.
 

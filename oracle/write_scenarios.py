@@ -99,6 +99,27 @@ def tgv(N=256, nu_reduced=1e-3):
                 Re=0.5 * math.sqrt(thermo.sound_speed_sq(rho0, T0, A_R, B, R_GAS, CV)) / nu_reduced)
 
 
+def strong_shock(D, Ma=1.47, nu=0.01):
+    """Planar Ma 1.47 shock into the supercritical vapour (rho 0.3, T 1.1), no drop.
+
+    The velocity scale keeps the second moment of the equilibrium away from
+    the lattice limit: U^2 is the smallest integer with
+    max(theta_r + u_r^2) / U^2 <= 0.27 over the states (the rule of the other
+    workloads, max theta_r / U^2 <= 1/4, leaves theta + u^2 = 0.35 behind a
+    Ma 1.47 shock, where the scheme is unstable).  Run with shock capturing.
+    """
+    vap = (0.3, 1.1)
+    r2, T2, u2, us = thermo.rankine_hugoniot(vap[0], vap[1], 0.0, Ma, A_R, B, R_GAS, CV)
+    U2 = float(math.ceil(max(_theta_r(*vap), _theta_r(r2, T2) + u2 * u2) / 0.27))
+    U = math.sqrt(U2)
+    eos = _lattice_eos(U2, kappa=0.01, eta_over_mu=1.0, rho_ref=vap[0], T_ref_r=vap[1])
+    return dict(D=D, U2=U2, cv=CV, Pr=0.71, nu=nu, eos=eos, tau=_tau(eos, nu), Ma=Ma,
+                vapour=dict(rho=vap[0], T=vap[1] / U2),
+                drop=dict(rho=1.8, T=thermo.temperature_from_pressure(1.8, thermo.pressure(*vap, A_R, B, R_GAS),
+                                                                      A_R, B, R_GAS) / U2),
+                post=dict(rho=r2, T=T2 / U2, u=u2 / U), shock_speed=us / U)
+
+
 def batch(n=256, seed=2025, Ma_lo=1.1, Ma_hi=1.3):
     """Uneven D2Q9 shock-tube instances for the batched form.
 
@@ -131,6 +152,8 @@ def main():
         shock_drop_d2q9=_shock_drop(2, 1.47, 0.01),
         tgv_d3q27=tgv(),
         shock_drop_d3q27=_shock_drop(3, 1.47, 0.01),
+        strong_shock_d2q9=strong_shock(2),
+        strong_shock_d3q27=strong_shock(3),
     )
     bt = batch()
     # parity cases: smaller noise amplitude reference sound speed per scenario

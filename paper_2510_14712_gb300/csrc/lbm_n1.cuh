@@ -18,16 +18,19 @@
 
 namespace lbm {
 
+// v mod n for a shift of at most a few nodes: one comparison in range
+__device__ __forceinline__ int n1_wrap(int v, int n) { return unsigned(v) < unsigned(n) ? v : modp(v, n); }
+
 // interior neighbour (x, y, z) + s e_a: wrapped, or clamped on a non-periodic x
 __device__ __forceinline__ long long n1_off(const Params& p, int x, int y, int z, int a, int s) {
   if (a == 0) {
     x += s;
-    if (p.periodic_x) x = modp(x, p.Nx);
+    if (p.periodic_x) x = n1_wrap(x, p.Nx);
     else x = x < 0 ? 0 : (x >= p.Nx ? p.Nx - 1 : x);
   } else if (a == 1) {
-    y = modp(y + s, p.Ny);
+    y = n1_wrap(y + s, p.Ny);
   } else {
-    z = modp(z + s, p.Nz);
+    z = n1_wrap(z + s, p.Nz);
   }
   return ((long long)z * p.Ny + y) * p.pitch + x + p.G;
 }
@@ -51,13 +54,17 @@ __global__ void k_n1_strain(Params p, const real* __restrict__ rho, const real* 
   int x, y, z;
   long long o;
   if (!n1_node(p, x, y, z, o)) return;
-  real g[D][D];                                    // g[a][b] = d_a u_b (central)
+  long long op[D], om[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const long long op = n1_off(p, x, y, z, a, 1), om = n1_off(p, x, y, z, a, -1);
-#pragma unroll
-    for (int b = 0; b < D; ++b) g[a][b] = real(0.5) * (u[b * p.plane + op] - u[b * p.plane + om]);
+    op[a] = n1_off(p, x, y, z, a, 1);
+    om[a] = n1_off(p, x, y, z, a, -1);
   }
+  real g[D][D];                                    // g[a][b] = d_a u_b (central)
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) g[a][b] = real(0.5) * (u[b * p.plane + op[a]] - u[b * p.plane + om[a]]);
   real acc = real(0);
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -69,8 +76,7 @@ __global__ void k_n1_strain(Params p, const real* __restrict__ rho, const real* 
   real gs2 = real(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const long long op = n1_off(p, x, y, z, a, 1), om = n1_off(p, x, y, z, a, -1);
-    const real gT = real(0.5) * (T[op] - T[om]), gr = real(0.5) * (rho[op] - rho[om]);
+    const real gT = real(0.5) * (T[op[a]] - T[om[a]]), gr = real(0.5) * (rho[op[a]] - rho[om[a]]);
     const real gs = cT * gT - cR * gr;
     gs2 += gs * gs;
   }
@@ -83,14 +89,21 @@ __global__ void k_n1_d4(Params p, const real* __restrict__ in, real* __restrict_
   int x, y, z;
   long long o;
   if (!n1_node(p, x, y, z, o)) return;
+  long long nb[D][4];                              // offsets of the -2, -1, +1, +2 neighbours along a
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    nb[a][0] = n1_off(p, x, y, z, a, -2);
+    nb[a][1] = n1_off(p, x, y, z, a, -1);
+    nb[a][2] = n1_off(p, x, y, z, a, 1);
+    nb[a][3] = n1_off(p, x, y, z, a, 2);
+  }
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
     const real* v = in + f * p.plane;
     real acc = real(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const real d4 = v[n1_off(p, x, y, z, a, 2)] - real(4) * v[n1_off(p, x, y, z, a, 1)] + real(6) * v[o] -
-                      real(4) * v[n1_off(p, x, y, z, a, -1)] + v[n1_off(p, x, y, z, a, -2)];
+      const real d4 = v[nb[a][3]] - real(4) * v[nb[a][2]] + real(6) * v[o] - real(4) * v[nb[a][1]] + v[nb[a][0]];
       acc += d4 * d4;
     }
     out[f * p.plane + o] = sqrt(acc);
@@ -103,12 +116,12 @@ __global__ void k_n1_filter(Params p, int a, const real* __restrict__ in, real* 
   int x, y, z;
   long long o;
   if (!n1_node(p, x, y, z, o)) return;
+  const long long m2 = n1_off(p, x, y, z, a, -2), m1 = n1_off(p, x, y, z, a, -1);
+  const long long p1 = n1_off(p, x, y, z, a, 1), p2 = n1_off(p, x, y, z, a, 2);
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
     const real* v = in + f * p.plane;
-    out[f * p.plane + o] = (v[n1_off(p, x, y, z, a, -2)] + real(4) * v[n1_off(p, x, y, z, a, -1)] +
-                            real(6) * v[o] + real(4) * v[n1_off(p, x, y, z, a, 1)] +
-                            v[n1_off(p, x, y, z, a, 2)]) / real(16);
+    out[f * p.plane + o] = (v[m2] + real(4) * v[m1] + real(6) * v[o] + real(4) * v[p1] + v[p2]) / real(16);
   }
 }
 

@@ -120,12 +120,12 @@ def acoustic_decay(L=64, nu=0.02, eta=1.0, Max=0.0):
     return sig, theory
 
 
-def shock_tube(Ma=1.2, Nx=400, steps=(100, 250), shock_capturing=None):
+def shock_tube(Ma=1.2, Nx=400, steps=(100, 250), shock_capturing=None, scenario="shock_drop_d2q9"):
     """Planar shock from the Rankine-Hugoniot post-state into vapour at rest (Sec. 4.4 states).
 
     Returns (speed measured, speed RH, plateau (rho, u, T) measured, RH post-state).
     """
-    sc = inputs.scenario("shock_drop_d2q9")
+    sc = inputs.scenario(scenario)
     eos = dict(sc["eos"])
     vap = sc["vapour"]
     r2, T2, u2, us = thermo.rankine_hugoniot(vap["rho"], vap["T"], 0.0, Ma,

@@ -156,3 +156,29 @@ def test_wide_3d_shock_stable_only_with_shock_capturing(P):
     print("plateau %.5f vs %.5f, speed %.4f vs %.4f" % (plateau, post[0], speed, us))
     assert abs(plateau / post[0] - 1) < 0.03, (plateau, post[0])
     assert abs(speed / us - 1) < 0.05, (speed, us)
+
+
+def test_ma147_3d_shock_runs_with_shock_capturing(P):
+    """The shock-drop workloads' Ma 1.47 shock (D3Q27, 768 x 32 x 32, U^2 = 16): the
+    plain scheme blows up within 100 steps, with shock capturing (C = 0.3) it runs
+    1000 steps and keeps about the Rankine-Hugoniot post-state."""
+    case = inputs.strong_shock(3, (768, 32, 32), seed=21)
+    s = P.Solver(case, precision="fp32").init()
+    with pytest.raises(P.LbmError):
+        s.step(200)
+    s.close()
+    s = P.Solver(case, precision="fp32")
+    P.lbm_set_shock_capturing(s.h, 0.3, 0.0, 0.3)
+    s.init()
+    s.step(1000)
+    F = s.fields()
+    s.close()
+    assert np.isfinite(F["rho"]).all()
+    r = F["rho"].mean(axis=(0, 1))
+    front = case.shape[0] - 1 - int(np.argmax(r[::-1] > 0.5 * (r[:300].mean() + 0.3)))
+    post = case.x_low[1][0]
+    plateau = F["rho"][:, :, 150:front - 60].mean()
+    sp = inputs.scenario("strong_shock_d3q27")["shock_speed"]
+    print("Ma 1.47: plateau %.4f vs %.4f, front %d vs %.0f" % (plateau, post, front, case.shape[0] // 8 + 1000 * sp))
+    assert abs(plateau / post - 1) < 0.03
+    assert abs(front - (case.shape[0] // 8 + 1000 * sp)) < 0.05 * 1000 * sp

@@ -131,3 +131,14 @@ def _post_sc(Ma):
     r2, T2, u2, us = thermo.rankine_hugoniot(vap["rho"], vap["T"], 0.0, Ma, e["a"], e["b"], e["R"], sc["cv"])
     sc["post"] = dict(rho=r2, T=T2, u=u2)
     return sc
+
+
+@pytest.mark.parametrize("coef", [None, (0.3, 0.0, 0.3)])
+def test_ma147_shock_at_the_larger_velocity_scale(coef):
+    """The shock-drop workloads' Ma 1.47 shock on the U^2 = 16 velocity scale keeps the
+    Rankine-Hugoniot plateau and speed, with and without the numerical transport."""
+    speed, us, plateau, post = pc.shock_tube(Ma=1.47, Nx=600, steps=(100, 300), shock_capturing=coef,
+                                             scenario="strong_shock_d2q9")
+    assert abs(speed / us - 1) < 0.02
+    for got, want in zip(plateau, post):
+        assert abs(got / want - 1) < 0.01
