@@ -47,13 +47,19 @@ WORKLOADS = {
     "strongshock3d": ("strong_shock", dict(D=3, shape=(512, 256, 256), seed=21), "fp32",
                       "D3Q27 shock tube 512x256x256 at the workloads' Ma 1.47 (U^2 = 16), shock capturing "
                       "C_mu = C_k = 0.3, FP32"),
+    "strongshock3d-mlp": ("strong_shock", dict(D=3, shape=(512, 256, 256), seed=21), "fp32",
+                          "D3Q27 shock tube 512x256x256 at Ma 1.47 (U^2 = 16), shock capturing C_mu = C_k = 0.3, "
+                          "learned closure (2-64-64-3 BF16 MLP), FP32"),
     "shocktube3d-mlp-small": ("shock_tube_3d", dict(shape=(256, 128, 128), Ma=1.15, seed=21), "fp32",
                               "D3Q27 shock tube 256x128x128 (Ma 1.15), learned closure, FP32 (profiling case)"),
 }
 # workloads whose step uses the learned closure, trained before the timed region
-MLP_WORKLOADS = {"shocktube3d-mlp", "shocktube3d-mlp-small"}
+# learned-closure workloads: training-run table, largest Mach number, scenario of the units
+MLP_WORKLOADS = {"shocktube3d-mlp": ("batch_d2q9", 1.25, "shock_drop_d3q27"),
+                 "shocktube3d-mlp-small": ("batch_d2q9", 1.25, "shock_drop_d3q27"),
+                 "strongshock3d-mlp": ("strong_posts_d2q9", 1.5, "strong_shock_d3q27")}
 # workloads that run with shock capturing (C_mu, C_eta, C_k)
-SC_WORKLOADS = {"strongshock3d": (0.3, 0.0, 0.3)}
+SC_WORKLOADS = {"strongshock3d": (0.3, 0.0, 0.3), "strongshock3d-mlp": (0.3, 0.0, 0.3)}
 MLP_TRAIN = dict(snapshots=50, every=20, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5, net_seed=11)
 BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # Longest run from the initial state that stays finite, per (builder, precision):
@@ -326,7 +332,7 @@ def run_ours(args):
     closure_info, net = None, None
     if args.workload in MLP_WORKLOADS:
         # same case with the exact closure first: tuned, then timed like the main loop
-        net, closure_info = train_closure(P, dev, case)
+        net, closure_info = train_closure(P, dev, args.workload)
         if not args.no_autotune:
             P.lbm_autotune(solver.h, 3)
         P.lbm_step(solver.h, args.warmup)
@@ -472,16 +478,17 @@ def run_ours(args):
     return 0
 
 
-def train_closure(P, dev, case):
+def train_closure(P, dev, workload):
     """Train the learned closure on solver states (GPU), untimed; returns (net, info)."""
     import numpy as np
     import torch
     import inputs
     t0 = time.perf_counter()
-    sc = inputs.scenario("shock_drop_d3q27")
+    table, Ma_max, units = MLP_WORKLOADS[workload]
+    sc = inputs.scenario(units)
     net = P.Closure(sc["eos"]["a"], sc["eos"]["b"], sc["eos"]["R"], sc["cv"], seed=MLP_TRAIN["net_seed"])
-    rho, e = net.collect_runs(inputs.closure_training_runs(), MLP_TRAIN["snapshots"], MLP_TRAIN["every"],
-                              precision="fp32")
+    rho, e = net.collect_runs(inputs.closure_training_runs(table=table, Ma_max=Ma_max), MLP_TRAIN["snapshots"],
+                              MLP_TRAIN["every"], precision="fp32", shock_capturing=SC_WORKLOADS.get(workload))
     net.fit_scaling(rho, e)
     losses = net.train(rho, e, batch=MLP_TRAIN["batch"], steps=MLP_TRAIN["steps"], lr0=MLP_TRAIN["lr0"],
                        lr1=MLP_TRAIN["lr1"], seed=MLP_TRAIN["seed"])

@@ -230,7 +230,7 @@ def strong_shock(D=3, shape=(768, 32, 32), seed=None, rel=1e-3):
     return c
 
 
-def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25):
+def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25, table="batch_d2q9"):
     """(case, e_scale) runs whose states train the learned closure.
 
     The D2Q9 Riemann problem and ``n_tubes`` narrow D2Q9 shock tubes (shock
@@ -240,16 +240,20 @@ def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25):
     transverse instability within 1000 steps without shock capturing.
     Energies are brought to the lattice units of the shock scenarios
     (velocity scale squared U^2 = 12): e_scale = U^2(run) / U^2(shock) for
-    the Riemann problem.
+    the Riemann problem.  With table="strong_posts_d2q9" the tubes are those
+    of the strong_shock scenario (U^2 = 16, Ma 1.1 .. 1.5; run them with shock
+    capturing) and the Riemann energies are brought to U^2 = 16.
     """
-    tab = scenario("batch_d2q9")["instances"]
+    tab_all = scenario(table)
+    tab = tab_all["instances"]
     order = sorted((i for i in range(len(tab)) if tab[i]["Ma"] <= Ma_max), key=lambda i: tab[i]["Ma"])
     pick = [order[int(round(j * (len(order) - 1) / max(n_tubes - 1, 1)))] for j in range(n_tubes)]
-    base = scenario("shock_drop_d2q9")
+    base = scenario(tab_all["base"])
     runs = [(add_noise(riemann(), seed), scenario("riemann_d2q9")["U2"] / base["U2"])]
     for j, k in enumerate(pick):
         sc = dict(base)
         sc["post"] = tab[k]["post"]
         c = shock_drop(2, (Nx, Ny), shock_x=Nx // 4, with_drop=False, sc=sc)
+        c.name = tab_all["base"]
         runs.append((add_noise(c, seed + 1 + 4 * j), 1.0))
     return runs

@@ -120,6 +120,20 @@ def strong_shock(D, Ma=1.47, nu=0.01):
                 post=dict(rho=r2, T=T2 / U2, u=u2 / U), shock_speed=us / U)
 
 
+def strong_posts(n=13, Ma_lo=1.1, Ma_hi=1.5):
+    """RH post-states of shocks Ma_lo .. Ma_hi into the vapour, in the lattice units of
+    the strong_shock scenarios (U^2 = 16): the learned closure's training runs there."""
+    sc = strong_shock(2)
+    vap = (0.3, 1.1)
+    U = math.sqrt(sc["U2"])
+    out = []
+    for k in range(n):
+        Ma = Ma_lo + (Ma_hi - Ma_lo) * k / (n - 1)
+        r2, T2, u2, us = thermo.rankine_hugoniot(vap[0], vap[1], 0.0, Ma, A_R, B, R_GAS, CV)
+        out.append(dict(Ma=Ma, post=dict(rho=r2, T=T2 / sc["U2"], u=u2 / U)))
+    return dict(base="strong_shock_d2q9", instances=out)
+
+
 def batch(n=256, seed=2025, Ma_lo=1.1, Ma_hi=1.3):
     """Uneven D2Q9 shock-tube instances for the batched form.
 
@@ -165,6 +179,7 @@ def main():
         else:
             sc["cs_ref"] = sc["cs"]
     out["batch_d2q9"] = bt
+    out["strong_posts_d2q9"] = strong_posts()
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "inputs", "scenarios.json")
     with open(path, "w") as fh:

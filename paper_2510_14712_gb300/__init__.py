@@ -552,12 +552,16 @@ class Closure:
         lbm_mlp_collect(solver.h, rho, e, e_scale)
         return rho, e
 
-    def collect_runs(self, runs, snapshots, every, precision="fp64"):
-        """Run each (case, e_scale) for snapshots * every steps and collect every `every` steps."""
+    def collect_runs(self, runs, snapshots, every, precision="fp64", shock_capturing=None):
+        """Run each (case, e_scale) for snapshots * every steps and collect every `every` steps
+        (optionally with shock capturing (C_mu, C_eta, C_k))."""
         import torch
         rs, es = [], []
         for case, e_scale in runs:
-            s = Solver(case, precision).init()
+            s = Solver(case, precision)
+            if shock_capturing:
+                lbm_set_shock_capturing(s.h, *shock_capturing)
+            s.init()
             for _ in range(snapshots):
                 s.step(every)
                 r, e = self.collect(s, e_scale)

@@ -264,3 +264,40 @@ def test_mlp_argument_errors(P):
     out = net.predict(r, r)
     assert out.shape == (4, 4)
     net.close()
+
+
+@pytest.fixture(scope="module")
+def trained_strong(P):
+    """A network trained on the Riemann problem and 12 D2Q9 tubes of Ma 1.1 .. 1.5 on the
+    U^2 = 16 scale of the Ma 1.47 workload, run with shock capturing."""
+    sc = inputs.scenario("strong_shock_d3q27")
+    net = P.Closure(sc["eos"]["a"], sc["eos"]["b"], sc["eos"]["R"], sc["cv"], seed=11)
+    runs = inputs.closure_training_runs(table="strong_posts_d2q9", Ma_max=1.5)
+    rho, e = net.collect_runs(runs, snapshots=50, every=20, precision="fp32", shock_capturing=(0.3, 0.0, 0.3))
+    net.fit_scaling(rho, e)
+    net.train(rho, e, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5)
+    yield net
+    net.close()
+
+
+def test_learned_closure_ma147_shock_d3q27(P, trained_strong):
+    """The workloads' Ma 1.47 shock (D3Q27 768 x 32 x 32, shock capturing, 1000 steps)
+    with the learned closure stays finite and within 1e-2 (relative L2 of rho) of the
+    exact closure in FP64.  The strong shock amplifies any perturbation: the exact
+    closure in FP32 is already 9e-4 away from FP64 here (the 1e-3 bar is met at
+    Ma 1.15, test_learned_closure_shock_tube_d3q27)."""
+    case = inputs.strong_shock(3, (768, 32, 32), seed=21)
+    out = {}
+    for name, prec, net in (("ref", "fp64", None), ("ex32", "fp32", None), ("mlp", "fp32", trained_strong)):
+        s = P.Solver(case, precision=prec)
+        P.lbm_set_shock_capturing(s.h, 0.3, 0.0, 0.3)
+        if net is not None:
+            net.attach(s)
+        s.init().step(1000)
+        out[name] = s.fields()
+        s.close()
+    err = rel_l2(out["mlp"]["rho"], out["ref"]["rho"])
+    err32 = rel_l2(out["ex32"]["rho"], out["ref"]["rho"])
+    print("Ma 1.47 rho rel L2 vs exact fp64: learned %.3e, exact fp32 %.3e" % (err, err32))
+    assert np.isfinite(out["mlp"]["rho"]).all()
+    assert err <= 1e-2, err
