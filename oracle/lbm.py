@@ -258,7 +258,21 @@ class Model:
     """Constants of one run: lattice, vdW parameters, transport and boundaries.
 
     eos: dict with a, b, R (lattice units), kappa, eta_over_mu, rho_ref, T_ref.
-    x_low / x_high: "periodic", "outflow" or ("inflow", (rho, u_vector, T)).
+    x_low / x_high: "periodic", "outflow", ("inflow", (rho, u_vector, T)) or
+    ("wall", (u_vector, T)): a wall moving with velocity u at temperature T
+    (the thermal Couette flow of Sec. 4.1; the paper gives no wall scheme).
+    Reading: diffuse reflection.  The wall re-emits the mass that reaches it
+    from the first fluid layer with the equilibrium at (u_wall, T_wall): the
+    ghost layers of a wall face hold s f^eq, s g^eq at (rho_e, u_wall, T_wall),
+    rho_e the density of the first fluid node and s = (sum of its
+    post-collision f that stream into the wall) / (sum of those f^eq that
+    stream out of it).  f^eq is not linear in rho (theta = P/rho), so the
+    shape is taken at rho_e and scaled: a wall at rest at the fluid's own
+    state re-emits that state's equilibrium, and no mass crosses the wall.
+    The Laplacian of the Korteweg force sees the wall as a symmetry plane
+    (capillary_density): with the ghost layers' own density s rho_e in it, the
+    flux-balance factor s feeds the capillary stencil and an odd-even mode
+    grows from the wall.
     """
 
     def __init__(self, D, shape, eos, tau, Pr, cv, x_low="periodic", x_high="periodic"):
@@ -351,9 +365,36 @@ class Sim:
         edge = np.take(q, [0 if first else -1], axis=ax)
         if spec == "outflow":
             return edge
-        kind, (rho_b, u_b, T_b) = spec
+        kind, state = spec
+        if kind == "wall":
+            u_w, T_w = state
+            if k == 0:
+                return edge                          # density: nearest interior node
+            return np.full_like(edge, float((list(u_w) + [T_w])[k - 1]))
+        rho_b, u_b, T_b = state
         val = ([rho_b] + list(u_b) + [T_b])[k]
         return np.full_like(edge, float(val))
+
+    def capillary_density(self, rho):
+        """Density seen by the Laplacian of the Korteweg force (Eq. FK): rho itself,
+        except in the ghost layers of a wall face, which hold the mirror image of the
+        fluid across the wall (ghost x = G - 1 - k takes fluid x = G + k): the wall
+        is a symmetry plane of the capillary terms (neutral wetting)."""
+        m = self.m
+        walls = [(spec, lo) for spec, lo in ((m.x_low, True), (m.x_high, False))
+                 if spec not in ("periodic", "outflow") and spec[0] == "wall"]
+        if not walls:
+            return rho
+        ax, G, Nx = m.ax(0), m.G, m.shape[0]
+        out = rho.copy()
+        for spec, lo in walls:
+            for k in range(G):
+                xg, xs = (G - 1 - k, G + k) if lo else (G + Nx + k, G + Nx - 1 - k)
+                dst = [slice(None)] * m.D
+                src = [slice(None)] * m.D
+                dst[ax], src[ax] = xg, xs
+                out[tuple(dst)] = rho[tuple(src)]
+        return out
 
     # -- flow chart steps 1-3 ------------------------------------------------
     def macroscopic(self, f=None, g=None):
@@ -365,7 +406,8 @@ class Sim:
         rho = f.sum(axis=0)                                           # Eq. def_h
         j = [first_moment(f, m.c, a) for a in range(D)]
         S = g.sum(axis=0)
-        lap = sum(m.nb(rho, a, 1) - 2.0 * rho + m.nb(rho, a, -1) for a in range(D))
+        rk = self.capillary_density(rho)
+        lap = sum(m.nb(rk, a, 1) - 2.0 * rk + m.nb(rk, a, -1) for a in range(D))
         F = [m.kappa * rho * 0.5 * (m.nb(lap, a, 1) - m.nb(lap, a, -1)) for a in range(D)]
         u = velocity(j, F, rho)                                        # Eq. def_u
         uF = sum(u[a] * F[a] for a in range(D))
@@ -449,15 +491,41 @@ class Sim:
         gpost = self.g + 2.0 * beta * (geq - self.g) + (1.0 - beta) * (gst - geq)
         return fpost, gpost
 
-    def fill_ghosts(self, p, which):
-        """Refill the x ghost layers of post-collision populations p (f or g)."""
+    def wall_emission(self, fpost, src, sign, u_w, T_w):
+        """Ghost (f, g) of a diffuse-reflection wall next to fluid layer src: the
+        equilibrium at (rho_e, u_w, T_w) of that layer's density rho_e, scaled so
+        that the f it streams out of the wall (c_x = -sign) carry the mass of the
+        layer's post-collision f that stream into it (c_x = sign)."""
+        m = self.m
+        ax = m.ax(0) + 1
+        layer = np.take(fpost, src, axis=ax)                     # [Q, transverse...]
+        rho_e = layer.sum(axis=0)
+        fb, gb = m.state_eq(rho_e, [np.full_like(rho_e, float(x)) for x in u_w],
+                            np.full_like(rho_e, float(T_w)))
+        into = sum(layer[i] for i, ci in enumerate(m.c) if ci[0] == sign)
+        out = sum(fb[i] for i, ci in enumerate(m.c) if ci[0] == -sign)
+        s = into / out
+        return fb * s, gb * s
+
+    def fill_ghosts(self, p, which, fpost=None):
+        """Refill the x ghost layers of post-collision populations p (f or g); wall faces
+        take their density from the post-collision f (fpost, or p itself for f)."""
         m = self.m
         if m.periodic_x:
             return
         G, Nx = m.G, m.shape[0]
         ax = m.ax(0) + 1                       # +1: leading population axis
-        for spec, ghosts, src in ((m.x_low, range(0, G), G),
-                                  (m.x_high, range(G + Nx, 2 * G + Nx), G + Nx - 1)):
+        for spec, ghosts, src, sign in ((m.x_low, range(0, G), G, -1),
+                                        (m.x_high, range(G + Nx, 2 * G + Nx), G + Nx - 1, 1)):
+            if spec != "outflow" and spec[0] == "wall":
+                u_w, T_w = spec[1]
+                fb, gb = self.wall_emission(p if fpost is None else fpost, src, sign, u_w, T_w)
+                val = fb if which == "f" else gb
+                for xg in ghosts:
+                    dst = [slice(None)] * (m.D + 1)
+                    dst[ax] = xg
+                    p[tuple(dst)] = val
+                continue
             for xg in ghosts:
                 dst = [slice(None)] * (m.D + 1)
                 dst[ax] = xg
@@ -485,8 +553,8 @@ class Sim:
     def step(self, n=1):
         for _ in range(n):
             fpost, gpost = self.collide()
+            self.fill_ghosts(gpost, "g", fpost)      # before f: a wall's density comes from fpost
             self.fill_ghosts(fpost, "f")
-            self.fill_ghosts(gpost, "g")
             self.f = self.stream(fpost)
             self.g = self.stream(gpost)
             self.t += 1

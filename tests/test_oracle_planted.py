@@ -91,3 +91,48 @@ def test_wrong_psi_rest_factor_breaks_weights(monkeypatch):
     import test_oracle_equilibria as te
     with pytest.raises(AssertionError):
         te.test_weights_at_rest(3)
+
+
+def unit_density_emission(self, fpost, src, sign, u_w, T_w):
+    """Wall re-emitting at rho_w = into / (outgoing f^eq at unit density): f^eq is not
+    linear in rho (theta = P / rho), so this does not balance the mass flux."""
+    m = self.m
+    layer = np.take(fpost, src, axis=m.ax(0) + 1)
+    f1, _ = m.state_eq(np.float64(1.0), [np.float64(x) for x in u_w], np.float64(T_w))
+    into = sum(layer[i] for i, ci in enumerate(m.c) if ci[0] == sign)
+    out = sum(f1[i] for i, ci in enumerate(m.c) if ci[0] == -sign)
+    rw = into / out
+    return m.state_eq(rw, [np.full_like(rw, float(x)) for x in u_w], np.full_like(rw, float(T_w)))
+
+
+def test_unit_density_wall_emission_breaks_mass_pin(monkeypatch):
+    import test_oracle_walls as tw
+    monkeypatch.setattr(lbm.Sim, "wall_emission", unit_density_emission)
+    with pytest.raises(AssertionError):
+        tw.test_walls_conserve_mass()
+
+
+def test_swapped_wall_direction_breaks_mass_pin(monkeypatch):
+    import test_oracle_walls as tw
+    orig = lbm.Sim.wall_emission
+    monkeypatch.setattr(lbm.Sim, "wall_emission",
+                        lambda self, fpost, src, sign, u_w, T_w: orig(self, fpost, src, -sign, u_w, T_w))
+    with pytest.raises(AssertionError):
+        tw.test_walls_conserve_mass()
+
+
+def test_wrong_ghost_source_layer_breaks_mirror_pin(monkeypatch):
+    import test_oracle_walls as tw
+    orig = lbm.Sim.wall_emission
+    monkeypatch.setattr(lbm.Sim, "wall_emission",
+                        lambda self, fpost, src, sign, u_w, T_w: orig(self, fpost, src + (1 if sign < 0 else 0),
+                                                                     sign, u_w, T_w))
+    with pytest.raises(AssertionError):
+        tw.test_faces_are_mirror_images()
+
+
+def test_ghost_density_in_capillary_stencil_breaks_odd_even_pin(monkeypatch):
+    import test_oracle_walls as tw
+    monkeypatch.setattr(lbm.Sim, "capillary_density", lambda self, rho: rho)
+    with pytest.raises(AssertionError):
+        tw.test_odd_even_disturbance_decays_next_to_walls()
