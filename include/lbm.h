@@ -70,7 +70,7 @@ enum {
 enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
 
 /* x-face boundary types */
-enum { LBM_BC_PERIODIC = 0, LBM_BC_OUTFLOW = 1, LBM_BC_INFLOW = 2 };
+enum { LBM_BC_PERIODIC = 0, LBM_BC_OUTFLOW = 1, LBM_BC_INFLOW = 2, LBM_BC_WALL = 3 };
 
 /* faces for lbm_set_boundary */
 enum { LBM_FACE_XLO = 0, LBM_FACE_XHI = 1 };
@@ -115,13 +115,24 @@ typedef struct {
 int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* eos,
                double tau, double Pr, double cv);
 
-/* Set the type of one x face before lbm_init.  state (for LBM_BC_INFLOW only)
- * points to D+2 doubles (rho, u_1..u_D, T) of the inflow state; otherwise
- * it may be NULL.  Setting one face to LBM_BC_PERIODIC sets both.  Changing
+/* Set the type of one x face before lbm_init.  state: for LBM_BC_INFLOW
+ * D+2 doubles (rho, u_1..u_D, T) of the inflow state; for LBM_BC_WALL D+1
+ * doubles (u_1..u_D, T) of the wall's velocity and temperature; otherwise it
+ * may be NULL.  Setting one face to LBM_BC_PERIODIC sets both.  Changing
  * between periodic and non-periodic after lbm_create re-lays out the device
  * state (the state must then be re-initialised).
- * Errors: LBM_EINVAL (bad face/type, NULL state for inflow, non-positive
- * rho or T), LBM_ENOMEM, LBM_ECUDA. */
+ *
+ * LBM_BC_WALL: a moving isothermal wall (the thermal Couette flow of Sec.
+ * 4.1; the paper gives no wall scheme, this is a diffuse-reflection
+ * reading).  After each collision the ghost layers of the face take
+ * s f^eq, s g^eq at (rho_e, u_wall, T_wall), rho_e the density of the first
+ * fluid node and s the ratio of that node's post-collision f streaming into
+ * the wall to the f^eq streaming out of it, so no mass crosses the wall.  The
+ * Laplacian of the Korteweg force (Eq. FK) sees the wall as a symmetry plane:
+ * a ghost column's density there is that of its mirror image in the fluid.
+ * The normal wall velocity u_1 should be 0.
+ * Errors: LBM_EINVAL (bad face/type, NULL state for inflow or wall,
+ * non-positive rho or T, a wall with Nx < 4), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_set_boundary(lbm_t h, int face, int type, const double* state);
 
 /* Use the given cudaStream_t (passed as void*) for all later work of this

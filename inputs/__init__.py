@@ -61,7 +61,7 @@ class Case:
     tau: float
     Pr: float
     cv: float
-    x_low: object = "periodic"   # "periodic" | "outflow" | ("inflow", (rho, u, T))
+    x_low: object = "periodic"   # "periodic" | "outflow" | ("inflow", (rho, u, T)) | ("wall", (u, T))
     x_high: object = "periodic"
     rho: np.ndarray = None
     u: list = field(default_factory=list)
@@ -225,6 +225,31 @@ def strong_shock(D=3, shape=(768, 32, 32), seed=None, rel=1e-3):
     name = "strong_shock_d2q9" if D == 2 else "strong_shock_d3q27"
     c = shock_drop(D, shape, shock_x=shape[0] // 8, with_drop=False, sc=scenario(name))
     c.name = name
+    if seed is not None:
+        add_noise(c, seed, rel)
+    return c
+
+
+def couette(D=2, shape=None, Ma=0.8, Pr=None, seed=None, rel=1e-3):
+    """Thermal Couette flow (Sec. 4.1, couette_d2q9 / _d3q27): walls at both x faces
+    at T_w, the one at x = Nx - 1 sliding along y at U_w = Ma c_s; the fluid at rest
+    at rho_ref, T_w; y (and z) periodic.  Default shape: the paper's 100 nodes
+    across, one node along the other axes (pseudo-one-dimensional).  Optional
+    seeded perturbation of relative size ``rel`` (add_noise)."""
+    name = "couette_d2q9" if D == 2 else "couette_d3q27"
+    sc = scenario(name)
+    shape = tuple(shape) if shape is not None else ((sc["Nx"], 1) if D == 2 else (sc["Nx"], 1, 1))
+    c = _base(name, sc, shape)
+    if Pr is not None:
+        c.Pr = Pr
+    zero = [0.0] * D
+    moving = [0.0] * D
+    moving[1] = Ma * sc["cs"]
+    c.x_low = ("wall", (zero, sc["T_w"]))
+    c.x_high = ("wall", (moving, sc["T_w"]))
+    c.rho = np.full(tuple(reversed(shape)), sc["rho"])
+    c.T = np.full(tuple(reversed(shape)), sc["T_w"])
+    c.u = [np.zeros_like(c.rho) for _ in range(D)]
     if seed is not None:
         add_noise(c, seed, rel)
     return c

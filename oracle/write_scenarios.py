@@ -56,6 +56,33 @@ def riemann():
                 left=dict(rho=left[0], T=left[1] / U2), right=dict(rho=right[0], T=right[1] / U2))
 
 
+def couette(D, nu=0.2, rho=0.65, T_r=1.15, Ma=(0.8, 1.2, 1.6), Ma_transverse=0.5):
+    """Thermal Couette flow (Sec. 4.1): a supercritical fluid at rest at (rho, T_w)
+    between two isothermal walls, one sliding at U_w = Ma c_s.  The paper's runs:
+    100 nodes, Pr in {0.6, 1.2, 4.9} at Ma 0.8 and Ma in {0.8, 1.2, 1.6} at Pr
+    1.2, pseudo-one-dimensional.  Lattice viscosity nu (the channel width fixes
+    the units).
+
+    Velocity scale: the rule of strong_shock, U^2 the smallest integer with
+    (theta_r + U_w,r^2) / U^2 <= 0.27, here for a wall at Ma_transverse.  The
+    fluid next to a sliding wall moves with it, and with transverse structure
+    (seeded noise, several nodes along y) a flow with theta + u^2 above about
+    1/3 is unstable in this scheme (a seeded periodic box: stable at 0.28 and
+    0.32, unstable at 0.34 and 0.35).  No integer scale brings the paper's
+    Ma 1.6 wall below that with theta >= 0.1, so its runs stay
+    pseudo-one-dimensional (one node along y), as the paper's case is: there
+    the transverse populations stay on their node and no transverse mode
+    exists."""
+    cs_r = math.sqrt(thermo.sound_speed_sq(rho, T_r, A_R, B, R_GAS, CV))
+    uw_r = Ma_transverse * cs_r
+    U2 = float(math.ceil((_theta_r(rho, T_r) + uw_r * uw_r) / 0.27))
+    eos = _lattice_eos(U2, kappa=0.01, eta_over_mu=1.0, rho_ref=rho, T_ref_r=T_r)
+    cs = _cs_lattice(eos["rho_ref"], eos["T_ref"], eos)
+    return dict(D=D, U2=U2, cv=CV, Pr=1.2, nu=nu, eos=eos, tau=_tau(eos, nu), cs=cs,
+                rho=eos["rho_ref"], T_w=eos["T_ref"], Nx=100,
+                Ma=list(Ma), Pr_runs=[0.6, 1.2, 4.9], Ma_transverse=Ma_transverse)
+
+
 def _shock_drop(D, Ma, nu):
     vap = (0.3, 1.1)
     rho_d = 1.8
@@ -168,6 +195,8 @@ def main():
         shock_drop_d3q27=_shock_drop(3, 1.47, 0.01),
         strong_shock_d2q9=strong_shock(2),
         strong_shock_d3q27=strong_shock(3),
+        couette_d2q9=couette(2),
+        couette_d3q27=couette(3),
     )
     bt = batch()
     # parity cases: smaller noise amplitude reference sound speed per scenario

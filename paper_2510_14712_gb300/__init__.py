@@ -21,7 +21,7 @@ LBM_D2Q9, LBM_D3Q27 = 9, 27
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
 LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
 LBM_CLOSURE_EXACT, LBM_CLOSURE_MLP = 0, 1
-LBM_BC_PERIODIC, LBM_BC_OUTFLOW, LBM_BC_INFLOW = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_OUTFLOW, LBM_BC_INFLOW, LBM_BC_WALL = 0, 1, 2, 3
 LBM_FACE_XLO, LBM_FACE_XHI = 0, 1
 LBM_FLAG_NONFINITE, LBM_FLAG_NEGATIVE, LBM_FLAG_THETA, LBM_FLAG_PRESSURE = 1, 2, 4, 8
 LBM_STEP_FUSED, LBM_STEP_MULTIPASS = 0, 1
@@ -169,6 +169,21 @@ def lbm_create(lattice, Nx, Ny, Nz, eos, tau, Pr, cv, precision="fp64", closure=
     h = ctypes.c_void_p()
     _check(lib.lbm_create(ctypes.byref(h), lattice, Nx, Ny, Nz, ctypes.byref(e), tau, Pr, cv))
     return h
+
+
+def face_args(spec, D):
+    """(LBM_BC_* type, state or None) of an x-face spec: "outflow",
+    ("inflow", (rho, u, T)) or ("wall", (u, T))."""
+    if spec == "outflow":
+        return LBM_BC_OUTFLOW, None
+    kind, state = spec
+    if kind == "inflow":
+        rb, ub, Tb = state
+        return LBM_BC_INFLOW, [rb] + list(ub)[:D] + [Tb]
+    if kind == "wall":
+        uw, Tw = state
+        return LBM_BC_WALL, list(uw)[:D] + [Tw]
+    raise ValueError("unknown face spec %r" % (spec,))
 
 
 def lbm_set_boundary(h, face, bctype, state=None):
@@ -326,13 +341,10 @@ class Batch:
             for face, spec in ((LBM_FACE_XLO, c.x_low), (LBM_FACE_XHI, c.x_high)):
                 if spec == "periodic":
                     continue
-                if spec == "outflow":
-                    _bcheck(lib.lbm_batch_set_boundary(self.b, k, face, LBM_BC_OUTFLOW, None))
-                else:
-                    _, (rb, ub, Tb) = spec
-                    st = np.ascontiguousarray([rb] + list(ub)[:self.D] + [Tb], dtype=np.float64)
-                    _bcheck(lib.lbm_batch_set_boundary(self.b, k, face, LBM_BC_INFLOW,
-                                                       st.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+                bctype, state = face_args(spec, self.D)
+                arr = None if state is None else np.ascontiguousarray(state, dtype=np.float64)
+                st = None if arr is None else arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                _bcheck(lib.lbm_batch_set_boundary(self.b, k, face, bctype, st))
 
     def init(self):
         lib = load()
@@ -498,11 +510,7 @@ class Solver:
         for face, spec in ((LBM_FACE_XLO, case.x_low), (LBM_FACE_XHI, case.x_high)):
             if spec == "periodic":
                 continue
-            if spec == "outflow":
-                lbm_set_boundary(self.h, face, LBM_BC_OUTFLOW)
-            else:
-                _, (rb, ub, Tb) = spec
-                lbm_set_boundary(self.h, face, LBM_BC_INFLOW, [rb] + list(ub)[:self.D] + [Tb])
+            lbm_set_boundary(self.h, face, *face_args(spec, self.D))
 
     def init(self, rho=None, u=None, T=None):
         c = self.case

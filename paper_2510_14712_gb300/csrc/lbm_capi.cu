@@ -309,7 +309,7 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
 int lbm_set_boundary(lbm_t h, int face, int type, const double* state) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (face != LBM_FACE_XLO && face != LBM_FACE_XHI) return fail(LBM_EINVAL, "face must be XLO or XHI");
-  if (type != LBM_BC_PERIODIC && type != LBM_BC_OUTFLOW && type != LBM_BC_INFLOW)
+  if (type != LBM_BC_PERIODIC && type != LBM_BC_OUTFLOW && type != LBM_BC_INFLOW && type != LBM_BC_WALL)
     return fail(LBM_EINVAL, "bad boundary type");
   Params& p = h->p;
   const int was_periodic = p.periodic_x;
@@ -326,6 +326,15 @@ int lbm_set_boundary(lbm_t h, int face, int type, const double* state) {
       for (int a = 0; a < h->D; ++a) st[1 + a] = state[1 + a];
       st[4] = state[h->D + 1];
       set_face_eq(*h, face);
+    }
+    if (type == LBM_BC_WALL) {
+      if (!state) return fail(LBM_EINVAL, "wall needs a state");
+      if (!(state[h->D] > 0)) return fail(LBM_EINVAL, "wall T must be > 0");
+      if (h->Nx < 4) return fail(LBM_EINVAL, "a wall face needs Nx >= 4 (mirror of the ghost layers)");
+      double* st = face == 0 ? p.st_lo : p.st_hi;
+      st[0] = st[1] = st[2] = st[3] = 0.0;      // st[0] unused: the wall density follows the fluid
+      for (int a = 0; a < h->D; ++a) st[1 + a] = state[a];
+      st[4] = state[h->D];
     }
     if (was_periodic) {  // the other face becomes outflow until set
       p.bc_lo = p.bc_hi = LBM_BC_OUTFLOW;

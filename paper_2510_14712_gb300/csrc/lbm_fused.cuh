@@ -44,9 +44,12 @@ template <int D, int TX, int TY, int EX = 0> struct FusedGeom {
   // centre ring on the tile only (read at the node): rho, F[D] (, P, c_s^2), two planes
   static constexpr int NCEN = 1 + D + EX;
   static constexpr int C_RHO = 0, C_F = 1, C_P = 1 + D, C_CS2 = 2 + D;
-  // bytes of the four rings, rounded up to 16 (a closure's table follows them)
+  // own density of the two R1 ghost columns next to wall faces (x = -1, Nx),
+  // three planes: the density ring holds their mirror images instead
+  static constexpr int NGOWN = 3 * 2 * BY1;
+  // bytes of the rings, rounded up to 16 (a closure's table follows them)
   template <typename real> static constexpr size_t smem_bytes() {
-    return (sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1 + 2 * NCEN * NT) + 15) &
+    return (sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1 + 2 * NCEN * NT + NGOWN) + 15) &
            ~size_t(15);
   }
 };
@@ -125,6 +128,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   real* s_lap = s_mom + 3 * G::NMOM * G::N1;                  // [3][N2]
   real* s_prm = s_lap + 3 * G::N2;                            // [3][NPRIM][N1]
   real* s_cen = s_prm + 3 * G::NPRIM * G::N1;                 // [2][NCEN][NT]
+  real* s_gown = s_cen + 2 * G::NCEN * G::NT;                 // [3][2][BY1]
 
   const Model<real> m = model_of<real>(p);
   const int tid = threadIdx.x;
@@ -177,6 +181,21 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           for (int a = 0; a < D; ++a) {
             if (L::c(i, a) == 1) sp[a] += v;
             if (L::c(i, a) == -1) sn[a] += v;
+          }
+        }
+        const int gw = wall_mirror(p, gx);
+        if (gw != gx) {
+          // ghost column of a wall face: the Laplacian reads the density of the
+          // mirror image (pulled here the same way as at that node); stage C
+          // reads the column's own density at x = -1 and x = Nx
+          if (in1 && (gx == -1 || gx == p.Nx))
+            s_gown[(slot * 2 + (gx < 0 ? 0 : 1)) * G::BY1 + ly - (G::HY3 - G::HY1)] = rho;
+          rho = real(0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
+            rho += Store<S>::template ld<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] +
+                                                               unsigned(gw + p.G - cx), p.ref[i]);
           }
         }
         s_rho[slot * G::N3 + k] = rho;
@@ -242,6 +261,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           const int k3 = (ly + (G::HY3 - G::HY1)) * G::BX3 + (lx + 2);
           const int k2 = (ly + (G::HY2 - G::HY1)) * G::BX2 + (lx + 1);
           rho = s_rho[sc * G::N3 + k3];
+          if (wall_mirror(p, gx) != gx) rho = s_gown[(sc * 2 + (gx < 0 ? 0 : 1)) * G::BY1 + ly];
           const real* lp = s_lap + sc * G::N2;
           F[0] = m.kappa * rho * real(0.5) * (lp[k2 + 1] - lp[k2 - 1]);                         // Eq. FK
           if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
@@ -479,7 +499,6 @@ k_step_fused_batch(const BatchInstance* __restrict__ insts, const BatchItem* __r
 // x faces are not periodic), as k_ghosts does for one instance.
 template <int D, typename S>
 __global__ void k_ghosts_batch(const BatchInstance* __restrict__ insts, int parity) {
-  using L = Lattice<D>;
   using ST = typename Store<S>::T;
   const BatchInstance& bi = insts[blockIdx.x];
   const Params& p = bi.p;
@@ -489,17 +508,7 @@ __global__ void k_ghosts_batch(const BatchInstance* __restrict__ insts, int pari
   for (long long gid = threadIdx.x; gid < n; gid += blockDim.x) {
     const int g = int(gid % (2 * p.G));
     const long long r = gid / (2 * p.G);
-    const int y = int(r % p.Ny), z = int(r / p.Ny);
-    const bool low = g < p.G;
-    const int xp = low ? g : p.Nx + g;
-    const int bc = low ? p.bc_lo : p.bc_hi;
-    const long long o = ((long long)z * p.Ny + y) * p.pitch + xp;
-    const long long os = ((long long)z * p.Ny + y) * p.pitch + (low ? p.G : p.G + p.Nx - 1);
-    const double* eq = low ? p.eq_lo : p.eq_hi;
-    for (int i = 0; i < 2 * L::Q; ++i) {
-      if (bc == LBM_BC_INFLOW) Store<S>::template st<double>(Bp, i * p.plane + o, eq[i], p.ref[i]);
-      else Bp[i * p.plane + o] = Bp[i * p.plane + os];
-    }
+    ghost_node<D, S>(p, Bp, g, int(r % p.Ny), int(r / p.Ny));
   }
 }
 

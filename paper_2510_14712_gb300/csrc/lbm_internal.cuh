@@ -25,7 +25,8 @@ struct Params {
   int bc_lo, bc_hi;           // LBM_BC_* of the x faces
   // model (FP64 master copy)
   double a, b, R, cv, kappa, eta_over_mu, mu, k_over_mu;
-  // inflow states (rho, u[3], T) and their equilibria (post-collision ghosts)
+  // inflow states (rho, u[3], T) and their equilibria (post-collision ghosts);
+  // wall faces: (unused, u[3], T) of the wall
   double st_lo[5], st_hi[5];
   double eq_lo[54], eq_hi[54];   // f then g
   // FP16-deviation reference populations (f then g)

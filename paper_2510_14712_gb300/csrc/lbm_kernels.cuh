@@ -69,6 +69,16 @@ __device__ __forceinline__ int xpad(const Params& p, int xp_shifted) {
   return p.periodic_x ? wrap(xp_shifted, p.Nx) : xp_shifted;
 }
 
+// x of the node whose density the Laplacian of the Korteweg force (Eq. FK)
+// reads at interior coordinate gx: gx itself, or its mirror image across a
+// wall face when gx is a ghost column of that face (the wall is a symmetry
+// plane of the capillary terms)
+__host__ __device__ __forceinline__ int wall_mirror(const Params& p, int gx) {
+  if (gx < 0 && p.bc_lo == LBM_BC_WALL) return -1 - gx;
+  if (gx >= p.Nx && p.bc_hi == LBM_BC_WALL) return 2 * p.Nx - 1 - gx;
+  return gx;
+}
+
 // decode a linear index over [xlo, xhi) x Ny x Nz (padded x)
 __device__ __forceinline__ bool decode(const Params& p, long long gid, int xlo, int xhi, int& xp, int& y, int& z) {
   const int nx = xhi - xlo;
@@ -83,18 +93,23 @@ __device__ __forceinline__ bool decode(const Params& p, long long gid, int xlo, 
 
 // Primitive state at interior coordinate (x, y, z) extended by the x-face
 // rules: inflow faces give their prescribed state, outflow faces the nearest
-// interior node, periodic wraps.  rho, u (D planes), T: interior FP64 fields.
+// interior node, wall faces the nearest interior node's density with the
+// wall's velocity and temperature, periodic wraps.  rho, u (D planes), T:
+// interior FP64 fields.
 template <int D>
 __device__ inline void prim_ext(const Params& p, const double* rho, const double* u, const double* T,
                                 int x, int y, int z, double& r, double* uu, double& t) {
   const long long N = (long long)p.Nx * p.Ny * p.Nz;
   const double* st = nullptr;
+  const double* wall = nullptr;
   if (p.periodic_x) {
     x = wrap(x, p.Nx);
   } else if (x < 0) {
     if (p.bc_lo == LBM_BC_INFLOW) st = p.st_lo; else x = 0;
+    if (p.bc_lo == LBM_BC_WALL) wall = p.st_lo;
   } else if (x >= p.Nx) {
     if (p.bc_hi == LBM_BC_INFLOW) st = p.st_hi; else x = p.Nx - 1;
+    if (p.bc_hi == LBM_BC_WALL) wall = p.st_hi;
   }
   if (st) {
     r = st[0];
@@ -104,8 +119,8 @@ __device__ inline void prim_ext(const Params& p, const double* rho, const double
   }
   const long long n = x + (long long)p.Nx * (y + (long long)p.Ny * z);
   r = rho[n];
-  for (int a = 0; a < D; ++a) uu[a] = u[a * N + n];
-  t = T[n];
+  for (int a = 0; a < D; ++a) uu[a] = wall ? wall[1 + a] : u[a * N + n];
+  t = wall ? wall[4] : T[n];
 }
 
 // ---------------------------------------------------------------------------
@@ -194,13 +209,16 @@ __device__ __forceinline__ long long nb_off(const Params& p, int xp, int y, int 
   return node_off(p, xp, y, wrap(z + s, p.Nz));
 }
 
-// compact Laplacian of rho at (xp, y, z)
+// compact Laplacian of rho at (xp, y, z); ghost columns of a wall face read
+// their mirror image (wall_mirror)
 template <int D, typename real>
 __device__ __forceinline__ real lap_rho(const Params& p, const real* rho, int xp, int y, int z) {
-  const real c = rho[node_off(p, xp, y, z)];
-  real l = 0;
+  const int xc = wall_mirror(p, xp - p.G) + p.G;
+  const real c = rho[node_off(p, xc, y, z)];
+  const int xr = wall_mirror(p, xpad(p, xp + 1) - p.G) + p.G, xl = wall_mirror(p, xpad(p, xp - 1) - p.G) + p.G;
+  real l = rho[node_off(p, xr, y, z)] - real(2) * c + rho[node_off(p, xl, y, z)];
 #pragma unroll
-  for (int a = 0; a < D; ++a) l += rho[nb_off(p, xp, y, z, a, 1)] - real(2) * c + rho[nb_off(p, xp, y, z, a, -1)];
+  for (int a = 1; a < D; ++a) l += rho[nb_off(p, xc, y, z, a, 1)] - real(2) * c + rho[nb_off(p, xc, y, z, a, -1)];
   return l;
 }
 
@@ -303,29 +321,61 @@ __global__ void k_collide(Params p, const typename Store<S>::T* A, typename Stor
 }
 
 // ---------------------------------------------------------------------------
-// ghost fill of the post-collision buffer (non-periodic x only): inflow faces
-// get the stored equilibria of their state, outflow faces copy the nearest
-// interior layer.  Thread per (ghost layer, y, z).
+// ghost fill of the post-collision buffer (non-periodic x only), one ghost
+// node (layer g of the 2G, row y, z): inflow faces get the stored equilibria
+// of their state, outflow faces copy the nearest interior node, wall faces
+// re-emit the mass that the nearest interior node sends into the wall with
+// the equilibrium of the wall (diffuse reflection): s f^eq, s g^eq at
+// (rho_e, u_wall, T_wall), rho_e that node's density, s = (its f with c_x
+// towards the wall) / (the f^eq with c_x away from it).  Reads only the
+// interior nodes next to the faces, so ghost nodes may be filled in any order.
 // ---------------------------------------------------------------------------
 template <int D, typename S>
-__global__ void k_ghosts(Params p, typename Store<S>::T* B) {
+__device__ inline void ghost_node(const Params& p, typename Store<S>::T* B, int g, int y, int z) {
   using L = Lattice<D>;
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long n = 2LL * p.G * p.Ny * p.Nz;
-  if (gid >= n) return;
-  const int g = int(gid % (2 * p.G));
-  const long long r = gid / (2 * p.G);
-  const int y = int(r % p.Ny), z = int(r / p.Ny);
   const bool low = g < p.G;
   const int xp = low ? g : p.Nx + g;
   const int bc = low ? p.bc_lo : p.bc_hi;
   const long long o = node_off(p, xp, y, z);
   const long long os = node_off(p, low ? p.G : p.G + p.Nx - 1, y, z);
+  if (bc == LBM_BC_WALL) {
+    const int towards = low ? -1 : 1;
+    double rho_e = 0.0, into = 0.0;
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = Store<S>::template ld<double>(B, i * p.plane + os, p.ref[i]);
+      rho_e += v;
+      if (L::c(i, 0) == towards) into += v;
+    }
+    const double* st = low ? p.st_lo : p.st_hi;
+    double uw[D], feq[L::Q], geq[L::Q];
+    for (int a = 0; a < D; ++a) uw[a] = st[1 + a];
+    equilibria<D, double>(model_of<double>(p), rho_e, uw, st[4], feq, geq);
+    double out = 0.0;
+    for (int i = 0; i < L::Q; ++i)
+      if (L::c(i, 0) == -towards) out += feq[i];
+    const double s = into / out;
+    for (int i = 0; i < L::Q; ++i) {
+      Store<S>::template st<double>(B, i * p.plane + o, s * feq[i], p.ref[i]);
+      Store<S>::template st<double>(B, (L::Q + i) * p.plane + o, s * geq[i], p.ref[L::Q + i]);
+    }
+    return;
+  }
   const double* eq = low ? p.eq_lo : p.eq_hi;
   for (int i = 0; i < 2 * L::Q; ++i) {
     if (bc == LBM_BC_INFLOW) Store<S>::template st<double>(B, i * p.plane + o, eq[i], p.ref[i]);
     else B[i * p.plane + o] = B[i * p.plane + os];
   }
+}
+
+// thread per (ghost layer, y, z)
+template <int D, typename S>
+__global__ void k_ghosts(Params p, typename Store<S>::T* B) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = 2LL * p.G * p.Ny * p.Nz;
+  if (gid >= n) return;
+  const int g = int(gid % (2 * p.G));
+  const long long r = gid / (2 * p.G);
+  ghost_node<D, S>(p, B, g, int(r % p.Ny), int(r / p.Ny));
 }
 
 // ---------------------------------------------------------------------------

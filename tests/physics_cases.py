@@ -177,6 +177,25 @@ def wall_channel(Nx=24, Ma=0.0, Pr=0.71, nu=0.2, perturb=0.0, moving="high"):
     return s, U_w, rho0, T_w
 
 
+def wall_channel(Nx=24, Ma=0.0, Pr=0.71, nu=0.2, perturb=0.0, moving="high"):
+    """D2Q9 channel between two walls at T_w (the couette_d2q9 fluid at rho_ref, T_w =
+    T_ref), one node in y, the `moving` wall ("high" or "low") sliding along y at
+    U_w = Ma c_s.  Initial state at rest at T_w with rho = rho_ref (1 + perturb sin x).
+    Returns (Sim, U_w, rho_ref, T_w)."""
+    sc = inputs.scenario("couette_d2q9")
+    eos = dict(sc["eos"])
+    rho0, T_w = eos["rho_ref"], eos["T_ref"]
+    cs = math.sqrt(thermo.sound_speed_sq(rho0, T_w, eos["a"], eos["b"], eos["R"], sc["cv"]))
+    U_w = Ma * cs
+    tau = nu * rho0 / thermo.pressure(rho0, T_w, eos["a"], eos["b"], eos["R"])
+    lo = ("wall", ([0.0, U_w if moving == "low" else 0.0], T_w))
+    hi = ("wall", ([0.0, U_w if moving == "high" else 0.0], T_w))
+    m = lbm.Model(2, (Nx, 1), eos, tau, Pr, sc["cv"], x_low=lo, x_high=hi)
+    rho = rho0 * (1.0 + perturb * np.sin(np.arange(Nx, dtype=float)))[None, :]
+    s = lbm.Sim(m, rho, [np.zeros((1, Nx)), np.zeros((1, Nx))], np.full((1, Nx), T_w))
+    return s, U_w, rho0, T_w
+
+
 def thermal_couette(Nx=24, Ma=0.5, Pr=0.71, nu=0.2, steps=6000):
     """Thermal Couette flow (Sec. 4.1): walls at both x faces at T_w, the upper one moving
     with U_w = Ma c_s along y; D2Q9, one node in y.  Returns (x, u_y, T, rho, U_w, T_w, mu, k)
