@@ -135,6 +135,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   const int Nm = D == 3 ? p.Nz : p.Ny;                        // march extent
   const long long mstride = D == 3 ? (long long)p.Ny * p.pitch : (long long)p.pitch;
   const int xmin = p.periodic_x ? -0x40000000 : -3, xmax = p.periodic_x ? 0x40000000 : p.Nx + 2;
+  // the column's R3 box reaches a ghost column of a wall face (block-uniform)
+  const bool wtile = (p.bc_lo == LBM_BC_WALL && x0 < 3) || (p.bc_hi == LBM_BC_WALL && x0 + TX + 3 > p.Nx);
   using ST = typename Store<S>::T;
   // element offsets inside a population buffer fit 32 bits (checked at create)
   const unsigned plane32 = unsigned(p.plane), pitch32 = unsigned(p.pitch);
@@ -183,7 +185,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
             if (L::c(i, a) == -1) sn[a] += v;
           }
         }
-        const int gw = wall_mirror(p, gx);
+        const int gw = wtile ? wall_mirror(p, gx) : gx;
         if (gw != gx) {
           // ghost column of a wall face: the Laplacian reads the density of the
           // mirror image (pulled here the same way as at that node); stage C
@@ -261,7 +263,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           const int k3 = (ly + (G::HY3 - G::HY1)) * G::BX3 + (lx + 2);
           const int k2 = (ly + (G::HY2 - G::HY1)) * G::BX2 + (lx + 1);
           rho = s_rho[sc * G::N3 + k3];
-          if (wall_mirror(p, gx) != gx) rho = s_gown[(sc * 2 + (gx < 0 ? 0 : 1)) * G::BY1 + ly];
+          if (wtile && wall_mirror(p, gx) != gx) rho = s_gown[(sc * 2 + (gx < 0 ? 0 : 1)) * G::BY1 + ly];
           const real* lp = s_lap + sc * G::N2;
           F[0] = m.kappa * rho * real(0.5) * (lp[k2 + 1] - lp[k2 - 1]);                         // Eq. FK
           if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
