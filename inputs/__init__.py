@@ -141,6 +141,21 @@ def shock_drop(D=2, shape=(4096, 2048), radius=128, center=None, shock_x=512,
     return c
 
 
+def shock_column(D=2, shape=(800, 800), radius=65, center=None, shock_x=None, width=3.0, seed=None, rel=1e-3):
+    """The paper's shock-liquid column (column_d2q9 / column_d3q27): saturated liquid
+    column (2-D) or sphere (3-D) at T_r 0.9 in its saturated vapour, Ma 1.47 planar
+    shock; default 800 x 800 with radius 65 as in the paper.  Shock at Nx/8 and
+    centre at (Nx/4, mid) unless given; tanh interface of `width` nodes; optional
+    seeded perturbation.  Run with the scenario's shock capturing."""
+    name = "column_d2q9" if D == 2 else "column_d3q27"
+    c = shock_drop(D, shape, radius=radius, center=center,
+                   shock_x=shape[0] // 8 if shock_x is None else shock_x, width=width, sc=scenario(name))
+    c.name = name
+    if seed is not None:
+        add_noise(c, seed, rel)
+    return c
+
+
 def tgv(N=256, shape=None):
     """D3Q27 periodic Taylor-Green vortex at constant density.
 
