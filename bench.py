@@ -47,6 +47,10 @@ WORKLOADS = {
                     "(U^2 = 35), shock capturing C_mu = C_k = 0.3, FP32"),
     "batched": ("batch", dict(), "fp32",
                 "256 uneven D2Q9 shock tubes (128x64 .. 1024x512, Ma 1.1-1.3), one persistent launch per step, FP32"),
+    "batched-drops": ("batch_columns", dict(), "fp32",
+                      "256 uneven D2Q9 instances (128x64 .. 1024x512), about half with a liquid column (radius 9-64), "
+                      "Ma 1.1-1.5 shocks, saturated liquid/vapour at T_r 0.9 (U^2 = 35), shock capturing C_mu = C_k "
+                      "= 0.3 in the batched step, one graph launch per step, FP32"),
     "shocktube3d-mlp": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
                         "D3Q27 shock tube 512x256x256 (Ma 1.15), learned closure (2-64-64-3 BF16 MLP), FP32"),
     "shocktube3d": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
@@ -67,7 +71,8 @@ MLP_WORKLOADS = {"shocktube3d-mlp": ("batch_d2q9", 1.25, "shock_drop_d3q27"),
                  "strongshock3d-mlp": ("strong_posts_d2q9", 1.5, "strong_shock_d3q27")}
 # workloads that run with shock capturing (C_mu, C_eta, C_k)
 SC_WORKLOADS = {"strongshock3d": (0.3, 0.0, 0.3), "strongshock3d-mlp": (0.3, 0.0, 0.3),
-                "shockdrop2d": (0.3, 0.0, 0.3), "column2d": (0.3, 0.0, 0.3), "shockdrop3d": (0.3, 0.0, 0.3)}
+                "shockdrop2d": (0.3, 0.0, 0.3), "column2d": (0.3, 0.0, 0.3), "shockdrop3d": (0.3, 0.0, 0.3),
+                "batched-drops": (0.3, 0.0, 0.3)}
 MLP_TRAIN = dict(snapshots=50, every=20, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5, net_seed=11)
 BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # Longest run from the initial state that stays finite, per (builder, precision):
@@ -77,8 +82,11 @@ BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # The shock-column runs stay finite to about t / t0 = 0.85 (1860 steps on the 4096 x
 # 2048 grid: the rarefaction reflected at the column's rear drives the liquid to
 # negative pressure), so they too are timed in chunks.
+# In the batched shock-drop table the smallest columns (128 x 64, radius 14, Ma ~1.5)
+# reach their outflow face within 500-750 steps, where the zero-gradient outflow
+# fails.
 MAX_CHUNK = {("tgv", "fp32"): 200, ("tgv", "fp16dev"): 100, ("tgv", "fp64"): 400, ("strong_shock", "fp32"): 500,
-             ("shock_column", "fp32"): 1500}
+             ("shock_column", "fp32"): 1500, ("batch_columns", "fp32"): 400}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16-storage/f32"}
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_fused.cuh", "lbm_mlp.cuh", "lbm_capi.cu"]
 
@@ -213,6 +221,12 @@ def _oracle_sample(workload, seconds, steps=None, warmup=1):
     elif builder == "batch":
         case = inputs.batch(1)[0]
         sample = "D2Q9 shock tube %dx%d (instance 0 of the batch), FP64 oracle" % case.shape
+    elif builder == "batch_columns":
+        tab = inputs.scenario("batch_columns_d2q9")["instances"]
+        k = min((d["Nx"] * d["Ny"], k) for k, d in enumerate(tab) if d["radius"] > 0)[1]
+        case = inputs.batch_columns(k + 1)[k]
+        sample = ("D2Q9 shock-liquid column %dx%d (instance %d of the batch, the smallest with a column) with shock "
+                  "capturing, FP64 oracle" % (case.shape + (k,)))
     elif builder == "shock_tube_3d":
         case = inputs.shock_tube_3d(shape=(128, 8, 8), Ma=kw["Ma"], seed=kw["seed"])
         sample = "D3Q27 shock tube 128x8x8 down-scale, exact closure, FP64 oracle"
@@ -275,24 +289,38 @@ def run_batched(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    cases = inputs.batch()
+    builder = WORKLOADS[args.workload][0]
+    cases = getattr(inputs, builder)()
     prec = args.precision or "fp32"
     b = P.Batch(cases, precision=prec)
     P._bcheck(P.load().lbm_batch_set_stream(b.b, ctypes_void_p(stream.cuda_stream)))
+    sc_coef = SC_WORKLOADS.get(args.workload)
+    if sc_coef:
+        b.set_shock_capturing(*sc_coef)
     b.init()
     tile = b.autotune(3)
     N = b.nodes()
-    b.step(args.warmup)
+    # chunks of at most `chunk` steps from the initial state (re-initialised outside the timing)
+    chunk = MAX_CHUNK.get((builder, prec), 1 << 30)
+    b.step(min(args.warmup, chunk))
     torch.cuda.synchronize(dev)
-    l0 = b.launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    b.step_async(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    b.sync()
-    ms = ev0.elapsed_time(ev1)
-    launches = b.launches() - l0
+    ms, done, launches, nchunks = 0.0, 0, 0, 0
+    while done < args.steps:
+        k = min(chunk, args.steps - done)
+        if nchunks > 0 or min(args.warmup, chunk) + k > chunk:
+            b.init()
+            torch.cuda.synchronize(dev)
+        l0 = b.launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.step_async(k)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        b.sync()
+        ms += ev0.elapsed_time(ev1)
+        launches += b.launches() - l0
+        done += k
+        nchunks += 1
     alg = sum(4 * c.lattice * BYTES[prec] * c.nodes for c in cases)
     achieved = alg / (ms * 1e-3 / args.steps) / 1e9
     peak, peak_kind = measured_peaks()
@@ -300,12 +328,16 @@ def run_batched(args):
     line = {"metric": "MLUPS", "value": N * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
-            "config": {"workload": WORKLOADS["batched"][3], "nodes": N, "instances": len(cases),
-                       "tile_shape": tile[0], "graph_captured": True},
+            "config": {"workload": WORKLOADS[args.workload][3], "nodes": N, "instances": len(cases),
+                       "tile_shape": tile[0], "graph_captured": True, "shock_capturing": sc_coef,
+                       "timed_chunk_steps": min(chunk, args.steps)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "batched step (persistent fused kernel + ghost fill)",
+                         "traffic": None, "kernel": "batched step (persistent fused kernel + ghost fill%s)"
+                         % (" + batched shock-capturing stencils" if sc_coef else ""),
                          "algorithmic_bytes_per_step": alg, "peak_source": peak_kind},
             "e2e": None, "gpu_launches": launches}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_leg(args.workload)
     print(json.dumps(line))
     return 0
 
@@ -538,7 +570,7 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batched":
+    if WORKLOADS[args.workload][0] in ("batch", "batch_columns"):
         return run_batched(args)
     return run_ours(args)
 

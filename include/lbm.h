@@ -265,6 +265,11 @@ int lbm_batch_create(lbm_batch_t* out, int lattice, int n, const int* Nx, const 
                      const lbm_eos* eos, double tau, double Pr, double cv);
 /* lbm_set_boundary for instance k. */
 int lbm_batch_set_boundary(lbm_batch_t b, int k, int face, int type, const double* state);
+/* lbm_set_shock_capturing for instance k, or for every instance with k = -1.
+ * The batched step then runs the shock-capturing stencils (Sec. 4.4) of all
+ * instances with it on in D + 2 further launches per step, one block per row
+ * of those instances.  Errors: as lbm_set_shock_capturing, LBM_EINVAL (bad k). */
+int lbm_batch_set_shock_capturing(lbm_batch_t b, int k, double C_mu, double C_eta, double C_k);
 /* Use a caller stream (non-NULL) instead of the batch's own. */
 int lbm_batch_set_stream(lbm_batch_t b, void* stream);
 /* lbm_init for instance k (host arrays); may be called at any step. */
@@ -287,7 +292,8 @@ int lbm_batch_flags(lbm_batch_t b, int k, unsigned* flags);
 int lbm_batch_autotune(lbm_batch_t b, int reps, int* chosen, float* ms_per_step);
 /* Interior nodes summed over the instances. */
 long long lbm_batch_nodes(lbm_batch_t b);
-/* Kernel launches enqueued by the batch's steps (2 per step). */
+/* Kernel launches enqueued by the batch's steps (2 per step, D + 4 with shock
+ * capturing on in any instance). */
 long long lbm_batch_launch_count(lbm_batch_t b);
 /* Free the batch and all its instances.  lbm_batch_destroy(NULL) is a no-op. */
 int lbm_batch_destroy(lbm_batch_t b);

@@ -199,6 +199,24 @@ def batch(n=None):
     return cases
 
 
+def batch_columns(n=None):
+    """The uneven D2Q9 instances of the batched shock-drop workload: shock tubes and
+    shock-liquid columns (radius > 0) from the stored table, in the fluid and units
+    of column_d2q9; equilibrium inflow at x = 0, zero-gradient outflow at x = Nx - 1.
+    Run with the scenario's shock capturing."""
+    tab = scenario("batch_columns_d2q9")
+    base = scenario(tab["base"])
+    cases = []
+    for d in tab["instances"][:n]:
+        sc = dict(base)
+        sc["post"] = d["post"]
+        r = d["radius"]
+        c = shock_drop(2, (d["Nx"], d["Ny"]), radius=max(r, 1), shock_x=d["shock_x"], with_drop=r > 0, sc=sc)
+        c.name = tab["base"]
+        cases.append(c)
+    return cases
+
+
 def add_noise(c, seed, rel=1e-3):
     """Seeded perturbation: rho *= 1 + rel U, u += rel c_ref U (U in [-1,1)).
 

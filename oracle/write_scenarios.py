@@ -224,6 +224,39 @@ def batch(n=256, seed=2025, Ma_lo=1.1, Ma_hi=1.3):
     return dict(base="shock_drop_d2q9", instances=out)
 
 
+def batch_columns(n=256, seed=2027, Ma_lo=1.1, Ma_hi=1.5, r_lo=8, r_hi=64):
+    """Uneven D2Q9 instances mixing shock tubes and shock-liquid columns for the
+    batched form with shock capturing, in the fluid and units of column_d2q9
+    (saturated vapour and liquid at T_r 0.9, U^2 = 35).
+
+    Nx uniform over the multiples of 64 in [128, 1024], Ny = Nx/2, Ma uniform in
+    [Ma_lo, Ma_hi], shock at x = Nx/8.  About half the instances hold a column
+    centred at (Nx/4, Ny/2) with radius uniform in [r_lo, r_hi], capped so that it
+    starts 2 nodes ahead of the shock and 4 nodes inside the y extent (radius 0:
+    a plain tube).  Draws come from the seeded generator of inputs/ (four
+    streams); each Rankine-Hugoniot post-state is computed here."""
+    import inputs
+    col = shock_column(2)
+    U2 = col["U2"]
+    U = math.sqrt(U2)
+    Tr = col["T_r"]
+    rv = col["vapour"]["rho"]
+    kx, km, kd, kr = (inputs.uniform(seed + j, n) for j in range(4))
+    out = []
+    for k in range(n):
+        nx = 64 * (2 + min(14, int((kx[k] + 1.0) * 0.5 * 15)))
+        ny = nx // 2
+        Ma = Ma_lo + (Ma_hi - Ma_lo) * (km[k] + 1.0) * 0.5
+        r2, T2, u2, us = thermo.rankine_hugoniot(rv, Tr, 0.0, Ma, A_R, B, R_GAS, CV)
+        radius = 0
+        if kd[k] < 0.0:
+            r = int(r_lo + (r_hi - r_lo) * (kr[k] + 1.0) * 0.5)
+            radius = max(r_lo, min(r, nx // 4 - nx // 8 - 2, ny // 2 - 4))
+        out.append(dict(Nx=nx, Ny=ny, Ma=Ma, shock_x=nx // 8, radius=radius,
+                        post=dict(rho=r2, T=T2 / U2, u=u2 / U), shock_speed=us / U))
+    return dict(base="column_d2q9", instances=out)
+
+
 def main():
     out = dict(
         riemann_d2q9=riemann(),
@@ -247,6 +280,7 @@ def main():
         else:
             sc["cs_ref"] = sc["cs"]
     out["batch_d2q9"] = bt
+    out["batch_columns_d2q9"] = batch_columns()
     out["strong_posts_d2q9"] = strong_posts()
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "inputs", "scenarios.json")

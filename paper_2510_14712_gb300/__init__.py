@@ -36,7 +36,8 @@ EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_
            "lbm_destroy",
            "lbm_last_error", "lbm_version",
            "lbm_totals_noalloc", "lbm_totals_noalloc_error",
-           "lbm_batch_create", "lbm_batch_set_boundary", "lbm_batch_set_stream", "lbm_batch_init",
+           "lbm_batch_create", "lbm_batch_set_boundary", "lbm_batch_set_shock_capturing", "lbm_batch_set_stream",
+           "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_moments", "lbm_batch_flags",
            "lbm_batch_autotune", "lbm_batch_nodes", "lbm_batch_launch_count", "lbm_batch_destroy",
            "lbm_batch_last_error",
@@ -103,6 +104,7 @@ def load():
         "lbm_batch_create": (I, [ctypes.POINTER(P), I, I, P, P, P, ctypes.POINTER(lbm_eos), D, D, D]),
         "lbm_batch_set_boundary": (I, [P, I, I, I, dp]),
         "lbm_batch_set_stream": (I, [P, P]),
+        "lbm_batch_set_shock_capturing": (I, [P, I, D, D, D]),
         "lbm_batch_init": (I, [P, I, P, P, P]),
         "lbm_batch_step": (I, [P, I]),
         "lbm_batch_step_async": (I, [P, I]),
@@ -357,6 +359,11 @@ class Batch:
 
     def step(self, n=1):
         _bcheck(load().lbm_batch_step(self.b, n))
+        return self
+
+    def set_shock_capturing(self, C_mu, C_eta, C_k, k=-1):
+        """Shock capturing for instance k (every instance with k = -1)."""
+        _bcheck(load().lbm_batch_set_shock_capturing(self.b, k, C_mu, C_eta, C_k))
         return self
 
     def step_async(self, n=1):

@@ -3,7 +3,8 @@
 // (own buffers, boundaries, moments); the batch adds a device table of the
 // instances, a work list of (instance, column, plane range) items sorted
 // longest first, and one CUDA graph per buffer parity holding a step:
-// counter reset, the persistent fused kernel, the batched ghost fill.
+// counter reset, the persistent fused kernel, the batched ghost fill and, when
+// any instance has shock capturing on, the batched shock-capturing stencils.
 #include <cstring>
 #include <new>
 #include <string>
@@ -55,6 +56,7 @@ int ready(Batch& b) {
     BCK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
     const long long l0 = b.launches;
     bops(b)->batch_enqueue(b, par);
+    b.graph_launches = int(b.launches - l0);   // kernel launches of one replay
     b.launches = l0;
     BCK(cudaStreamEndCapture(b.stream, &g));
     cudaError_t e = cudaGraphInstantiate(&b.graph[par], g, 0);
@@ -136,6 +138,16 @@ int lbm_batch_set_boundary(lbm_batch_t b, int k, int face, int type, const doubl
   return LBM_OK;
 }
 
+int lbm_batch_set_shock_capturing(lbm_batch_t b, int k, double C_mu, double C_eta, double C_k) {
+  if (!b || k < -1 || k >= b->n) return bfail(LBM_EINVAL, "bad batch or instance index");
+  for (int j = (k < 0 ? 0 : k); j < (k < 0 ? b->n : k + 1); ++j) {
+    const int rc = lbm_set_shock_capturing(static_cast<lbm_t>(b->inst[j]), C_mu, C_eta, C_k);
+    if (rc != LBM_OK) return bfail(rc, lbm_last_error());
+  }
+  b->graph_ready = 0;   // the instance table holds the coefficients and buffer pointers
+  return LBM_OK;
+}
+
 int lbm_batch_set_stream(lbm_batch_t b, void* stream) {
   if (!b || !stream) return bfail(LBM_EINVAL, "a batch needs a non-default stream");
   if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -174,7 +186,7 @@ int lbm_batch_step_async(lbm_batch_t b, int n) {
   if (rc != LBM_OK) return rc;
   for (int s = 0; s < n; ++s) {
     BCK(cudaGraphLaunch(b->graph[b->cur], b->stream));
-    b->launches += 2;
+    b->launches += b->graph_launches;
     b->cur ^= 1;
   }
   for (int k = 0; k < b->n; ++k) b->inst[k]->cur = b->cur;
@@ -217,11 +229,15 @@ int lbm_batch_autotune(lbm_batch_t b, int reps, int* chosen, float* ms_per_step)
   BCK(cudaEventCreate(&e1));
   int best = 0;
   float bt = 1e30f;
+  b->tuning = 1;                                             // tile shapes only change the fused step
   for (int c = 0; c < ncfg; ++c) {
     b->tile_cfg = c;
     b->graph_ready = 0;
     int rc = ready(*b);
-    if (rc != LBM_OK) return rc;
+    if (rc != LBM_OK) {
+      b->tuning = 0;
+      return rc;
+    }
     BCK(cudaGraphLaunch(b->graph[b->cur], b->stream));      // warm-up; writes the spare buffers only
     BCK(cudaEventRecord(e0, b->stream));
     for (int r = 0; r < reps; ++r) BCK(cudaGraphLaunch(b->graph[b->cur], b->stream));
@@ -236,6 +252,7 @@ int lbm_batch_autotune(lbm_batch_t b, int reps, int* chosen, float* ms_per_step)
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->tuning = 0;
   b->tile_cfg = best;
   b->graph_ready = 0;
   int rc = ready(*b);
@@ -264,6 +281,7 @@ int lbm_batch_destroy(lbm_batch_t b) {
       if (b->inst[k]) lbm_destroy(static_cast<lbm_t>(b->inst[k]));
   delete[] b->inst;
   if (b->d_insts) cudaFree(b->d_insts);
+  if (b->d_n1rows) cudaFree(b->d_n1rows);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->d_errs) cudaFree(b->d_errs);

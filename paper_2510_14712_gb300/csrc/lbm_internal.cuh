@@ -111,6 +111,11 @@ struct Batch {
   void* d_insts;              // device table of BatchInstance
   void* d_items;              // device work list of BatchItem, longest first
   int nitems;
+  int* d_n1rows;              // first global row of each instance's shock capturing (n + 1 entries)
+  int n1rows;                 // rows with shock capturing over all instances (0: none)
+  int graph_launches;         // kernel launches of one step's graph
+  int tuning;                 // graphs for timing tile shapes: no shock-capturing stencils (they would
+                              // overwrite the coefficients the next real step reads)
   int* d_counter;             // work-list counter of the persistent kernel
   unsigned* d_errs;           // status word per instance
   unsigned* h_errs;           // pinned copy

@@ -47,125 +47,201 @@ __device__ __forceinline__ unsigned n1_nb(const Params& p, int x, int y, int z, 
   return o + unsigned((n1_wrap(z + s, p.Nz) - z) * p.Ny * p.pitch);
 }
 
-// S and |grad s| of every interior node: out[0 .. plane) = S, out[plane ..) = |grad s|
+// ---- per-node stages (shared by the single-instance and batched kernels) ----
+
+// S and |grad s| at the node: out[0 .. plane) = S, out[plane ..) = |grad s|
 template <int D, typename real>
-__global__ void k_n1_strain(Params p, const real* __restrict__ rho, const real* __restrict__ u,
-                            const real* __restrict__ T, real* __restrict__ out) {
-  n1_rows(p, [&](const int x, const int y, const int z, const unsigned o) {
-    unsigned op[D], om[D];
+__device__ __forceinline__ void n1_strain_at(const Params& p, const real* __restrict__ rho,
+                                             const real* __restrict__ u, const real* __restrict__ T,
+                                             real* __restrict__ out, int x, int y, int z, unsigned o) {
+  unsigned op[D], om[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      op[a] = n1_nb(p, x, y, z, o, a, 1);
-      om[a] = n1_nb(p, x, y, z, o, a, -1);
-    }
-    real g[D][D];                                    // g[a][b] = d_a u_b (central)
+  for (int a = 0; a < D; ++a) {
+    op[a] = n1_nb(p, x, y, z, o, a, 1);
+    om[a] = n1_nb(p, x, y, z, o, a, -1);
+  }
+  real g[D][D];                                    // g[a][b] = d_a u_b (central)
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+  for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = 0; b < D; ++b) g[a][b] = real(0.5) * (u[b * p.plane + op[a]] - u[b * p.plane + om[a]]);
+    for (int b = 0; b < D; ++b) g[a][b] = real(0.5) * (u[b * p.plane + op[a]] - u[b * p.plane + om[a]]);
+  real acc = real(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) acc += (g[a][b] + g[b][a]) * (g[a][b] + g[b][a]);
+  out[o] = real(0.5) * sqrt(acc);
+  const real r = rho[o], t = T[o];
+  const real cR = real(p.R) / (r * (real(1) - real(p.b) * r)), cT = real(p.cv) / t;
+  real gs2 = real(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const real gT = real(0.5) * (T[op[a]] - T[om[a]]), gr = real(0.5) * (rho[op[a]] - rho[om[a]]);
+    const real gs = cT * gT - cR * gr;
+    gs2 += gs * gs;
+  }
+  out[p.plane + o] = sqrt(gs2);
+}
+
+// norm of the per-axis fourth differences of the two fields of `in` at the node
+template <int D, typename real>
+__device__ __forceinline__ void n1_d4_at(const Params& p, const real* __restrict__ in, real* __restrict__ out,
+                                         int x, int y, int z, unsigned o) {
+  unsigned nb[D][4];                               // offsets of the -2, -1, +1, +2 neighbours along a
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    nb[a][0] = n1_nb(p, x, y, z, o, a, -2);
+    nb[a][1] = n1_nb(p, x, y, z, o, a, -1);
+    nb[a][2] = n1_nb(p, x, y, z, o, a, 1);
+    nb[a][3] = n1_nb(p, x, y, z, o, a, 2);
+  }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    const real* v = in + f * p.plane;
     real acc = real(0);
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = 0; b < D; ++b) acc += (g[a][b] + g[b][a]) * (g[a][b] + g[b][a]);
-    out[o] = real(0.5) * sqrt(acc);
-    const real r = rho[o], t = T[o];
-    const real cR = real(p.R) / (r * (real(1) - real(p.b) * r)), cT = real(p.cv) / t;
-    real gs2 = real(0);
-#pragma unroll
     for (int a = 0; a < D; ++a) {
-      const real gT = real(0.5) * (T[op[a]] - T[om[a]]), gr = real(0.5) * (rho[op[a]] - rho[om[a]]);
-      const real gs = cT * gT - cR * gr;
-      gs2 += gs * gs;
+      const real d4 = v[nb[a][3]] - real(4) * v[nb[a][2]] + real(6) * v[o] - real(4) * v[nb[a][1]] + v[nb[a][0]];
+      acc += d4 * d4;
     }
-    out[p.plane + o] = sqrt(gs2);
-  });
+    out[f * p.plane + o] = sqrt(acc);
+  }
 }
 
-// norm of the per-axis fourth differences of the two fields of `in`
-template <int D, typename real>
-__global__ void k_n1_d4(Params p, const real* __restrict__ in, real* __restrict__ out) {
-  n1_rows(p, [&](const int x, const int y, const int z, const unsigned o) {
-    unsigned nb[D][4];                               // offsets of the -2, -1, +1, +2 neighbours along a
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      nb[a][0] = n1_nb(p, x, y, z, o, a, -2);
-      nb[a][1] = n1_nb(p, x, y, z, o, a, -1);
-      nb[a][2] = n1_nb(p, x, y, z, o, a, 1);
-      nb[a][3] = n1_nb(p, x, y, z, o, a, 2);
-    }
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const real* v = in + f * p.plane;
-      real acc = real(0);
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const real d4 = v[nb[a][3]] - real(4) * v[nb[a][2]] + real(6) * v[o] - real(4) * v[nb[a][1]] + v[nb[a][0]];
-        acc += d4 * d4;
-      }
-      out[f * p.plane + o] = sqrt(acc);
-    }
-  });
+// binomial (1, 4, 6, 4, 1)/16 along axis a of field f of `in` at the node
+template <typename real>
+__device__ __forceinline__ real n1_binomial(const Params& p, const real* __restrict__ in, int f, int a, int x, int y,
+                                            int z, unsigned o) {
+  const unsigned m2 = n1_nb(p, x, y, z, o, a, -2), m1 = n1_nb(p, x, y, z, o, a, -1);
+  const unsigned p1 = n1_nb(p, x, y, z, o, a, 1), p2 = n1_nb(p, x, y, z, o, a, 2);
+  const real* v = in + f * p.plane;
+  return (v[m2] + real(4) * v[m1] + real(6) * v[o] + real(4) * v[p1] + v[p2]) / real(16);
 }
 
-// binomial (1, 4, 6, 4, 1)/16 along axis a of the two fields of `in`
-template <int D, typename real>
-__global__ void k_n1_filter(Params p, int a, const real* __restrict__ in, real* __restrict__ out) {
-  n1_rows(p, [&](const int x, const int y, const int z, const unsigned o) {
-    const unsigned m2 = n1_nb(p, x, y, z, o, a, -2), m1 = n1_nb(p, x, y, z, o, a, -1);
-    const unsigned p1 = n1_nb(p, x, y, z, o, a, 1), p2 = n1_nb(p, x, y, z, o, a, 2);
+template <typename real>
+__device__ __forceinline__ void n1_filter_at(const Params& p, int a, const real* __restrict__ in,
+                                             real* __restrict__ out, int x, int y, int z, unsigned o) {
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const real* v = in + f * p.plane;
-      out[f * p.plane + o] = (v[m2] + real(4) * v[m1] + real(6) * v[o] + real(4) * v[p1] + v[p2]) / real(16);
-    }
-  });
+  for (int f = 0; f < 2; ++f) out[f * p.plane + o] = n1_binomial(p, in, f, a, x, y, z, o);
 }
 
 // the last filter pass (along axis D-1) and the coefficients from the filtered
-// norms in one pass: visc[0..2] planes = mu, eta, k numerical
+// norms: visc[0..2] planes = mu, eta, k numerical
 template <int D, typename real>
-__global__ void k_n1_filter_coef(Params p, const real* __restrict__ in, const real* __restrict__ rho,
-                                 const real* __restrict__ T, real* __restrict__ visc) {
+__device__ __forceinline__ void n1_filter_coef_at(const Params& p, const Model<real>& m, const real* __restrict__ in,
+                                                  const real* __restrict__ rho, const real* __restrict__ T,
+                                                  real* __restrict__ visc, int x, int y, int z, unsigned o) {
+  const real s4 = n1_binomial(p, in, 0, D - 1, x, y, z, o), g4 = n1_binomial(p, in, 1, D - 1, x, y, z, o);
+  const real r = rho[o];
+  const real cs2 = vdw_cs2(m, r, T[o]);
+  const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
+  visc[o] = r * real(p.sc_c[0]) * s4;
+  visc[p.plane + o] = r * real(p.sc_c[1]) * s4;
+  visc[2 * p.plane + o] = r * cs * real(p.sc_c[2]) * g4;
+}
+
+// Buffers of one handle's shock capturing: the step's rho, u (D planes), T (by
+// default the fused step's copy in sc_prims), the coefficients (3 planes)
+// followed by the work planes w0, w1 (2 each).  The stages run strain -> w0,
+// fourth differences w0 -> w1, filter passes alternating w1 -> w0 -> w1 ...,
+// the last pass with the coefficients.
+template <int D, typename real> struct N1Buffers {
+  const real *rho, *u, *T;
+  real *visc, *w0, *w1;
+  __host__ __device__ N1Buffers(const Params& p, const real* rho_, const real* u_, const real* T_)
+      : rho(rho_), u(u_), T(T_) {
+    visc = static_cast<real*>(const_cast<void*>(p.sc_visc));
+    w0 = visc + 3 * p.plane;
+    w1 = w0 + 2 * p.plane;
+  }
+  __host__ __device__ explicit N1Buffers(const Params& p)
+      : N1Buffers(p, static_cast<const real*>(p.sc_prims), static_cast<const real*>(p.sc_prims) + p.plane,
+                  static_cast<const real*>(p.sc_prims) + (1 + D) * p.plane) {}
+  // input of filter pass a (a = D - 1: the pass fused with the coefficients)
+  __host__ __device__ const real* filter_in(int a) const { return a % 2 == 0 ? w1 : w0; }
+  __host__ __device__ real* filter_out(int a) const { return a % 2 == 0 ? w0 : w1; }
+};
+
+// ---- single-instance kernels ----
+
+template <int D, typename real>
+__global__ void k_n1_strain(Params p, const real* __restrict__ rho, const real* __restrict__ u,
+                            const real* __restrict__ T) {
+  const N1Buffers<D, real> b(p, rho, u, T);
+  n1_rows(p, [&](int x, int y, int z, unsigned o) { n1_strain_at<D, real>(p, b.rho, b.u, b.T, b.w0, x, y, z, o); });
+}
+
+template <int D, typename real> __global__ void k_n1_d4(Params p) {
+  const N1Buffers<D, real> b(p);
+  n1_rows(p, [&](int x, int y, int z, unsigned o) { n1_d4_at<D, real>(p, b.w0, b.w1, x, y, z, o); });
+}
+
+template <int D, typename real> __global__ void k_n1_filter(Params p, int a) {
+  const N1Buffers<D, real> b(p);
+  n1_rows(p, [&](int x, int y, int z, unsigned o) { n1_filter_at<real>(p, a, b.filter_in(a), b.filter_out(a), x, y, z, o); });
+}
+
+template <int D, typename real>
+__global__ void k_n1_filter_coef(Params p, const real* __restrict__ rho, const real* __restrict__ T) {
+  const N1Buffers<D, real> b(p, rho, nullptr, T);
   const Model<real> m = model_of<real>(p);
-  n1_rows(p, [&](const int x, const int y, const int z, const unsigned o) {
-    constexpr int a = D - 1;
-    const unsigned m2 = n1_nb(p, x, y, z, o, a, -2), m1 = n1_nb(p, x, y, z, o, a, -1);
-    const unsigned p1 = n1_nb(p, x, y, z, o, a, 1), p2 = n1_nb(p, x, y, z, o, a, 2);
-    real fv[2];
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const real* v = in + f * p.plane;
-      fv[f] = (v[m2] + real(4) * v[m1] + real(6) * v[o] + real(4) * v[p1] + v[p2]) / real(16);
-    }
-    const real r = rho[o];
-    const real cs2 = vdw_cs2(m, r, T[o]);
-    const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
-    visc[o] = r * real(p.sc_c[0]) * fv[0];
-    visc[p.plane + o] = r * real(p.sc_c[1]) * fv[0];
-    visc[2 * p.plane + o] = r * cs * real(p.sc_c[2]) * fv[1];
+  n1_rows(p, [&](int x, int y, int z, unsigned o) {
+    n1_filter_coef_at<D, real>(p, m, b.filter_in(D - 1), b.rho, b.T, b.visc, x, y, z, o);
   });
 }
 
-// the whole update of the coefficients: rho, u (D planes), T -> visc (3 planes),
-// using work (4 planes); D + 2 launches
+// The whole update of a handle's coefficients from the step's rho, u (D planes),
+// T (padded plane layout): D + 2 launches.
 template <int D, typename real>
-inline int n1_update(const Params& p, cudaStream_t st, const real* rho, const real* u, const real* T, real* visc,
-                     real* work) {
+inline int n1_update(const Params& p, cudaStream_t st, const real* rho, const real* u, const real* T) {
   const dim3 block(128), grid(unsigned((p.Nx + 127) / 128), unsigned(p.Ny * p.Nz < 65535 ? p.Ny * p.Nz : 65535));
-  real* w0 = work;
-  real* w1 = work + 2 * p.plane;
-  k_n1_strain<D, real><<<grid, block, 0, st>>>(p, rho, u, T, w0);
-  k_n1_d4<D, real><<<grid, block, 0, st>>>(p, w0, w1);
-  real* src = w1;
-  real* dst = w0;
-  for (int a = 0; a + 1 < D; ++a) {
-    k_n1_filter<D, real><<<grid, block, 0, st>>>(p, a, src, dst);
-    real* t = src;
-    src = dst;
-    dst = t;
+  k_n1_strain<D, real><<<grid, block, 0, st>>>(p, rho, u, T);
+  k_n1_d4<D, real><<<grid, block, 0, st>>>(p);
+  for (int a = 0; a + 1 < D; ++a) k_n1_filter<D, real><<<grid, block, 0, st>>>(p, a);
+  k_n1_filter_coef<D, real><<<grid, block, 0, st>>>(p, rho, T);
+  return D + 2;
+}
+
+// ---- batched kernels: one block per row of every instance with shock capturing ----
+
+// rowstart[k] = first global row of instance k (prefix sum of Ny Nz over the
+// instances with shock capturing on, 0 rows for the others); rowstart[n] = total
+__device__ __forceinline__ int n1_instance(const int* __restrict__ rowstart, int n, int row) {
+  int lo = 0, hi = n;                              // largest k < n with rowstart[k] <= row
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (rowstart[mid] <= row) lo = mid;
+    else hi = mid;
   }
-  k_n1_filter_coef<D, real><<<grid, block, 0, st>>>(p, src, rho, T, visc);
+  return lo;
+}
+
+// stage 0: strain, 1: fourth differences, 2: filter pass a, 3: last pass + coefficients
+template <int D, typename real, int STAGE>
+__global__ void k_n1_batch(const BatchInstance* __restrict__ insts, const int* __restrict__ rowstart, int n, int a) {
+  const int k = n1_instance(rowstart, n, blockIdx.x);
+  const Params& p = insts[k].p;
+  const N1Buffers<D, real> b(p);
+  const int row = blockIdx.x - rowstart[k];
+  const int y = row % p.Ny, z = row / p.Ny;
+  const Model<real> m = model_of<real>(p);
+  for (int x = threadIdx.x; x < p.Nx; x += blockDim.x) {
+    const unsigned o = unsigned(row) * unsigned(p.pitch) + unsigned(x + p.G);
+    if constexpr (STAGE == 0) n1_strain_at<D, real>(p, b.rho, b.u, b.T, b.w0, x, y, z, o);
+    else if constexpr (STAGE == 1) n1_d4_at<D, real>(p, b.w0, b.w1, x, y, z, o);
+    else if constexpr (STAGE == 2) n1_filter_at<real>(p, a, b.filter_in(a), b.filter_out(a), x, y, z, o);
+    else n1_filter_coef_at<D, real>(p, m, b.filter_in(D - 1), b.rho, b.T, b.visc, x, y, z, o);
+  }
+}
+
+// the update of every instance with shock capturing on: D + 2 launches over
+// `rows` global rows
+template <int D, typename real>
+inline int n1_update_batch(const BatchInstance* insts, const int* rowstart, int n, int rows, cudaStream_t st) {
+  k_n1_batch<D, real, 0><<<rows, 128, 0, st>>>(insts, rowstart, n, 0);
+  k_n1_batch<D, real, 1><<<rows, 128, 0, st>>>(insts, rowstart, n, 0);
+  for (int a = 0; a + 1 < D; ++a) k_n1_batch<D, real, 2><<<rows, 128, 0, st>>>(insts, rowstart, n, a);
+  k_n1_batch<D, real, 3><<<rows, 128, 0, st>>>(insts, rowstart, n, D - 1);
   return D + 2;
 }
 

@@ -133,10 +133,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   // shock capturing: numerical mu, eta, k for the next step from this step's
   // rho, u (D planes), T
   static void shock_capturing(Handle& h, const real* rho, const real* u, const real* T) {
-    const Params& p = h.p;
-    real* visc = static_cast<real*>(const_cast<void*>(p.sc_visc));
-    real* work = visc + 3 * p.plane;
-    h.launches += n1_update<D, real>(p, h.stream, rho, u, T, visc, work);
+    h.launches += n1_update<D, real>(h.p, h.stream, rho, u, T);
   }
 
   template <class CL> static void step_cl(Handle& h, const void* src, void* dst) {
@@ -241,13 +238,22 @@ template <int D, typename S, typename real> struct OpsImpl {
       }
       std::stable_sort(items.begin(), items.end(),
                        [](const BatchItem& a, const BatchItem& c) { return a.me - a.mb > c.me - c.mb; });
+      // rows of the batched shock-capturing kernels: instances with it on
+      std::vector<int> rowstart(b.n + 1, 0);
+      for (int k = 0; k < b.n; ++k)
+        rowstart[k + 1] = rowstart[k] + (ti[k].p.sc_on ? ti[k].p.Ny * ti[k].p.Nz : 0);
       if (b.d_insts) cudaFree(b.d_insts);
       if (b.d_items) cudaFree(b.d_items);
+      if (b.d_n1rows) cudaFree(b.d_n1rows);
       b.d_insts = b.d_items = nullptr;
+      b.d_n1rows = nullptr;
       if (cudaMalloc(&b.d_insts, sizeof(BatchInstance) * b.n) != cudaSuccess) return LBM_ENOMEM;
       if (cudaMalloc(&b.d_items, sizeof(BatchItem) * items.size()) != cudaSuccess) return LBM_ENOMEM;
+      if (cudaMalloc(&b.d_n1rows, sizeof(int) * (b.n + 1)) != cudaSuccess) return LBM_ENOMEM;
       cudaMemcpy(b.d_insts, ti.data(), sizeof(BatchInstance) * b.n, cudaMemcpyHostToDevice);
       cudaMemcpy(b.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(b.d_n1rows, rowstart.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice);
+      b.n1rows = rowstart[b.n];
       b.nitems = int(items.size());
       const size_t smem = FG::template smem_bytes<real>();
       auto kern = k_step_fused_batch<D, S, real, TX, TY, MINB>;
@@ -267,6 +273,9 @@ template <int D, typename S, typename real> struct OpsImpl {
           parity, b.d_counter, b.d_errs);
       k_ghosts_batch<D, S><<<b.n, 256, 0, b.stream>>>(reinterpret_cast<const BatchInstance*>(b.d_insts), parity);
       b.launches += 2;
+      if (b.n1rows > 0 && !b.tuning)
+        b.launches += n1_update_batch<D, real>(reinterpret_cast<const BatchInstance*>(b.d_insts), b.d_n1rows, b.n,
+                                               b.n1rows, b.stream);
     }
   };
 

@@ -125,3 +125,76 @@ def test_batch_unstable_instance_is_reported_and_isolated():
         b.step(2)
     finally:
         b.close()
+
+
+def column_mix():
+    """Shock-liquid columns and a Ma 1.45 tube of the column fluid (the batched
+    shock-drop workload's), uneven sizes."""
+    from oracle import thermo
+    sc = copy.deepcopy(inputs.scenario("column_d2q9"))
+    e, v = sc["eos"], sc["vapour"]
+    r2, T2, u2, _ = thermo.rankine_hugoniot(v["rho"], v["T"], 0.0, 1.45, e["a"], e["b"], e["R"], sc["cv"])
+    sc["post"] = dict(rho=r2, T=T2, u=u2)
+    tube = inputs.shock_drop(2, (200, 64), shock_x=25, with_drop=False, sc=sc)
+    tube.name = "column_d2q9"
+    return [inputs.shock_column(2, (160, 96), radius=14, center=(45, 48), shock_x=20, seed=1), tube,
+            inputs.shock_column(2, (192, 100), radius=16, center=(50, 50), shock_x=24, seed=2),
+            inputs.shock_column(2, (130, 70), radius=10, center=(36, 35), shock_x=16, seed=3)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_shock_capturing_bit_identical_to_single_handles(precision):
+    """Shock capturing on instances 0-2 (not 3): the batched stencils, one block per
+    row of those instances, give each instance exactly its single-handle result."""
+    coef = tuple(inputs.scenario("column_d2q9")["shock_capturing"])
+    cases = column_mix()
+    b = P.Batch(cases, precision=precision)
+    try:
+        for k in range(3):
+            b.set_shock_capturing(*coef, k=k)
+        b.init().step(60)
+        got = [b.fields(k) for k in range(len(cases))]
+        assert b.launches() == 60 * (2 + 4)
+    finally:
+        b.close()
+    for k, c in enumerate(column_mix()):
+        s = P.Solver(c, precision=precision)
+        try:
+            if k < 3:
+                P.lbm_set_shock_capturing(s.h, *coef)
+            s.init().step(60)
+            want = s.fields()
+        finally:
+            s.close()
+        for f in ("rho", "u", "T"):
+            assert np.array_equal(got[k][f], want[f]), (k, f, rel_l2(got[k][f], want[f]))
+
+
+def test_batch_shock_capturing_bad_index():
+    b = P.Batch(column_mix()[:2], precision="fp32")
+    try:
+        with pytest.raises(P.LbmError):
+            b.set_shock_capturing(0.3, 0.0, 0.3, k=2)
+    finally:
+        b.close()
+
+
+def test_batch_autotune_with_shock_capturing_keeps_results():
+    """Timing the tile shapes must not touch the shock-capturing coefficients the next
+    step reads: a tuned batch steps bit-identically to an untuned one."""
+    coef = tuple(inputs.scenario("column_d2q9")["shock_capturing"])
+    runs = []
+    for tune in (False, True):
+        b = P.Batch(column_mix(), precision="fp32")
+        try:
+            b.set_shock_capturing(*coef)
+            b.init()
+            if tune:
+                b.autotune(2)
+            b.step(30)
+            runs.append([b.fields(k) for k in range(4)])
+        finally:
+            b.close()
+    for k in range(4):
+        for f in ("rho", "u", "T"):
+            assert np.array_equal(runs[0][k][f], runs[1][k][f]), (k, f)
