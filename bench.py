@@ -51,6 +51,10 @@ WORKLOADS = {
                       "256 uneven D2Q9 instances (128x64 .. 1024x512), about half with a liquid column (radius 9-64), "
                       "Ma 1.1-1.5 shocks, saturated liquid/vapour at T_r 0.9 (U^2 = 35), shock capturing C_mu = C_k "
                       "= 0.3 in the batched step, one graph launch per step, FP32"),
+    "shockdrop3d-mlp": ("shock_column", dict(D=3, shape=(512, 256, 256), radius=32), "fp32",
+                        "D3Q27 shock-drop 512x256x256: saturated liquid sphere radius 32 at T_r 0.9, Ma 1.47 shock "
+                        "(U^2 = 35), shock capturing C_mu = C_k = 0.3, learned closure (2-64-64-3 BF16 MLP trained on "
+                        "column and tube states of this fluid), FP32"),
     "shocktube3d-mlp": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
                         "D3Q27 shock tube 512x256x256 (Ma 1.15), learned closure (2-64-64-3 BF16 MLP), FP32"),
     "shocktube3d": ("shock_tube_3d", dict(shape=(512, 256, 256), Ma=1.15, seed=21), "fp32",
@@ -65,14 +69,16 @@ WORKLOADS = {
                               "D3Q27 shock tube 256x128x128 (Ma 1.15), learned closure, FP32 (profiling case)"),
 }
 # workloads whose step uses the learned closure, trained before the timed region
-# learned-closure workloads: training-run table, largest Mach number, scenario of the units
-MLP_WORKLOADS = {"shocktube3d-mlp": ("batch_d2q9", 1.25, "shock_drop_d3q27"),
-                 "shocktube3d-mlp-small": ("batch_d2q9", 1.25, "shock_drop_d3q27"),
-                 "strongshock3d-mlp": ("strong_posts_d2q9", 1.5, "strong_shock_d3q27")}
+# learned-closure workloads: training-run table, largest Mach number, scenario of the units,
+# number of 2-D shock-liquid column runs among the training runs
+MLP_WORKLOADS = {"shocktube3d-mlp": ("batch_d2q9", 1.25, "shock_drop_d3q27", 0),
+                 "shocktube3d-mlp-small": ("batch_d2q9", 1.25, "shock_drop_d3q27", 0),
+                 "strongshock3d-mlp": ("strong_posts_d2q9", 1.5, "strong_shock_d3q27", 0),
+                 "shockdrop3d-mlp": ("batch_columns_d2q9", 1.5, "column_d3q27", 3)}
 # workloads that run with shock capturing (C_mu, C_eta, C_k)
 SC_WORKLOADS = {"strongshock3d": (0.3, 0.0, 0.3), "strongshock3d-mlp": (0.3, 0.0, 0.3),
                 "shockdrop2d": (0.3, 0.0, 0.3), "column2d": (0.3, 0.0, 0.3), "shockdrop3d": (0.3, 0.0, 0.3),
-                "batched-drops": (0.3, 0.0, 0.3)}
+                "batched-drops": (0.3, 0.0, 0.3), "shockdrop3d-mlp": (0.3, 0.0, 0.3)}
 MLP_TRAIN = dict(snapshots=50, every=20, batch=8192, steps=60000, lr0=3e-3, lr1=1e-6, seed=5, net_seed=11)
 BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 # Longest run from the initial state that stays finite, per (builder, precision):
@@ -531,10 +537,11 @@ def train_closure(P, dev, workload):
     import torch
     import inputs
     t0 = time.perf_counter()
-    table, Ma_max, units = MLP_WORKLOADS[workload]
+    table, Ma_max, units, columns = MLP_WORKLOADS[workload]
     sc = inputs.scenario(units)
     net = P.Closure(sc["eos"]["a"], sc["eos"]["b"], sc["eos"]["R"], sc["cv"], seed=MLP_TRAIN["net_seed"])
-    rho, e = net.collect_runs(inputs.closure_training_runs(table=table, Ma_max=Ma_max), MLP_TRAIN["snapshots"],
+    runs = inputs.closure_training_runs(table=table, Ma_max=Ma_max, columns=columns)
+    rho, e = net.collect_runs(runs, MLP_TRAIN["snapshots"],
                               MLP_TRAIN["every"], precision="fp32", shock_capturing=SC_WORKLOADS.get(workload))
     net.fit_scaling(rho, e)
     losses = net.train(rho, e, batch=MLP_TRAIN["batch"], steps=MLP_TRAIN["steps"], lr0=MLP_TRAIN["lr0"],

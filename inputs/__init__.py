@@ -288,7 +288,7 @@ def couette(D=2, shape=None, Ma=0.8, Pr=None, seed=None, rel=1e-3):
     return c
 
 
-def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25, table="batch_d2q9"):
+def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25, table="batch_d2q9", columns=0):
     """(case, e_scale) runs whose states train the learned closure.
 
     The D2Q9 Riemann problem and ``n_tubes`` narrow D2Q9 shock tubes (shock
@@ -300,7 +300,11 @@ def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25, table
     (velocity scale squared U^2 = 12): e_scale = U^2(run) / U^2(shock) for
     the Riemann problem.  With table="strong_posts_d2q9" the tubes are those
     of the strong_shock scenario (U^2 = 16, Ma 1.1 .. 1.5; run them with shock
-    capturing) and the Riemann energies are brought to U^2 = 16.
+    capturing) and the Riemann energies are brought to U^2 = 16.  With
+    table="batch_columns_d2q9" the tubes are in the fluid and units of the
+    shock-liquid column (U^2 = 35, Ma 1.1 .. 1.5), and ``columns`` 2-D column
+    runs (512 x 256, radius 32, Ma 1.47, seeded) add liquid and interface
+    states; run them all with shock capturing.
     """
     tab_all = scenario(table)
     tab = tab_all["instances"]
@@ -314,4 +318,7 @@ def closure_training_runs(n_tubes=12, Nx=4096, Ny=4, seed=77, Ma_max=1.25, table
         c = shock_drop(2, (Nx, Ny), shock_x=Nx // 4, with_drop=False, sc=sc)
         c.name = tab_all["base"]
         runs.append((add_noise(c, seed + 1 + 4 * j), 1.0))
+    for j in range(columns):
+        c = shock_column(2, (512, 256), radius=32, center=(128, 128), shock_x=64, seed=seed + 101 + j)
+        runs.append((c, scenario(c.name)["U2"] / base["U2"]))
     return runs
