@@ -199,6 +199,25 @@ def batch(n=None):
     return cases
 
 
+def slab(T_r=0.95, Nx=256, kappa=None, width=3.0):
+    """Periodic D2Q9 slab (coexistence_d2q9): saturated liquid between x = Nx/4 and
+    3 Nx/4 in its saturated vapour at reduced temperature T_r (one of the table's),
+    tanh interfaces of `width` nodes, at rest, one node along y.  kappa: lattice
+    capillarity (default the table's)."""
+    tab = scenario("coexistence_d2q9")
+    st = tab["states"]["%.2f" % T_r]
+    eos = dict(st["eos"])
+    if kappa is not None:
+        eos["kappa"] = kappa
+    c = Case(name="coexistence_d2q9", D=2, shape=(Nx, 1), eos=eos, tau=st["tau"], Pr=tab["Pr"], cv=tab["cv"])
+    x = np.arange(Nx, dtype=np.float64)
+    prof = 0.5 * (np.tanh((x - Nx / 4) / width) - np.tanh((x - 3 * Nx / 4) / width))
+    c.rho = (st["rho_v"] + (st["rho_l"] - st["rho_v"]) * prof)[None, :]
+    c.T = np.full((1, Nx), st["T"])
+    c.u = [np.zeros((1, Nx)), np.zeros((1, Nx))]
+    return c
+
+
 def batch_columns(n=None):
     """The uneven D2Q9 instances of the batched shock-drop workload: shock tubes and
     shock-liquid columns (radius > 0) from the stored table, in the fluid and units

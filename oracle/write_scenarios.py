@@ -224,6 +224,24 @@ def batch(n=256, seed=2025, Ma_lo=1.1, Ma_hi=1.3):
     return dict(base="shock_drop_d2q9", instances=out)
 
 
+def coexistence(T_r=(0.85, 0.9, 0.95, 0.99), nu=0.01, kappa=0.1):
+    """Flat liquid-vapour equilibria (Sec. "Liquid-vapour co-existence"): for each
+    reduced temperature the Maxwell densities (the reference the paper compares
+    with) and the lattice units of a slab of saturated liquid in its saturated
+    vapour.  U^2 follows the liquid rule of shock_column (c_s^2(liquid) / U^2 <=
+    0.175; theta / U^2 <= 1/4); lattice viscosity nu, kappa the default lattice
+    capillarity (the interface spans about 2 sqrt(kappa / a) / sqrt(1 - T_r)
+    nodes).  Below T_r ~ 0.85 the slab does not run in this scheme."""
+    out = {}
+    for Tr in T_r:
+        rl, rv = thermo.maxwell_coexistence(Tr, A_R, B, R_GAS)
+        cs2_l = thermo.sound_speed_sq(rl, Tr, A_R, B, R_GAS, CV)
+        U2 = float(max(math.ceil(cs2_l / 0.175), _u2_for([(rl, Tr), (rv, Tr)])))
+        eos = _lattice_eos(U2, kappa=kappa, eta_over_mu=1.0, rho_ref=rv, T_ref_r=Tr)
+        out["%.2f" % Tr] = dict(U2=U2, eos=eos, tau=_tau(eos, nu), rho_l=rl, rho_v=rv, T=Tr / U2)
+    return dict(D=2, cv=CV, Pr=0.71, nu=nu, T_r=list(T_r), states=out)
+
+
 def batch_columns(n=256, seed=2027, Ma_lo=1.1, Ma_hi=1.5, r_lo=8, r_hi=64):
     """Uneven D2Q9 instances mixing shock tubes and shock-liquid columns for the
     batched form with shock capturing, in the fluid and units of column_d2q9
@@ -281,6 +299,7 @@ def main():
             sc["cs_ref"] = sc["cs"]
     out["batch_d2q9"] = bt
     out["batch_columns_d2q9"] = batch_columns()
+    out["coexistence_d2q9"] = coexistence()
     out["strong_posts_d2q9"] = strong_posts()
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "inputs", "scenarios.json")

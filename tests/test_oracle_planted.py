@@ -136,3 +136,21 @@ def test_ghost_density_in_capillary_stencil_breaks_odd_even_pin(monkeypatch):
     monkeypatch.setattr(lbm.Sim, "capillary_density", lambda self, rho: rho)
     with pytest.raises(AssertionError):
         tw.test_odd_even_disturbance_decays_next_to_walls()
+
+
+def test_korteweg_force_without_density_breaks_coexistence_pin(monkeypatch):
+    import test_oracle_coexistence as tc
+    orig = lbm.Sim.macroscopic
+
+    def without_rho(self, f=None, g=None):
+        m = self.m
+        kappa = m.kappa
+        m.kappa = kappa / (self.f if f is None else f).sum(axis=0)     # kappa rho grad lap rho -> kappa grad lap rho
+        try:
+            return orig(self, f, g)
+        finally:
+            m.kappa = kappa
+    monkeypatch.setattr(lbm.Sim, "macroscopic", without_rho)
+    import pytest as _pytest
+    with _pytest.raises(AssertionError):
+        tc.test_slab_plateaus_reach_maxwell_coexistence()
