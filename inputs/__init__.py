@@ -156,8 +156,9 @@ def shock_column(D=2, shape=(800, 800), radius=65, center=None, shock_x=None, wi
     return c
 
 
-def tgv(N=256, shape=None):
-    """D3Q27 periodic Taylor-Green vortex at constant density.
+def tgv(N=256, shape=None, scenario_name="tgv_d3q27"):
+    """D3Q27 periodic Taylor-Green vortex at constant density (tgv_d3q27, or the
+    Peng-Robinson fluid of tgv_pr_d3q27).
 
     u = U0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0), k = 2 pi / N per
     axis; T = T0 + T_amp (cos 2kx + cos 2ky)(cos 2kz + 2), the temperature that
@@ -165,9 +166,9 @@ def tgv(N=256, shape=None):
     The stored relaxation time is for the 256-node box; at fixed Reynolds
     number it scales with the box length in nodes (taken along x).
     """
-    sc = scenario("tgv_d3q27")
+    sc = scenario(scenario_name)
     shape = (N, N, N) if shape is None else tuple(shape)
-    c = _base("tgv_d3q27", sc, shape)
+    c = _base(scenario_name, sc, shape)
     c.tau = sc["tau"] * shape[0] / sc["N"]
     x, y, z = c.grid()
     kx, ky, kz = (2 * np.pi / n for n in shape)

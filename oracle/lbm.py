@@ -47,6 +47,7 @@ import itertools
 
 import numpy as np
 
+from . import eos as eos_pr
 from . import thermo
 
 CS2 = 1.0 / 3.0          # lattice speed of sound squared (Eq. cs)
@@ -216,13 +217,18 @@ def strain_rate_magnitude(u, D, per):
     return 0.5 * np.sqrt(sum((g[a][b] + g[b][a]) ** 2 for a in range(D) for b in range(D)))
 
 
-def entropy_gradient_magnitude(rho, T, b, R, cv, D, per):
-    """|grad s| with grad s = (c_v/T) grad T - R/(rho (1 - b rho)) grad rho (van der Waals)."""
+def entropy_gradient_magnitude(rho, T, b, R, cv, D, per, fluid=None):
+    """|grad s| with grad s = (c_v/T) grad T - R/(rho (1 - b rho)) grad rho (van der Waals);
+    for another fluid (an object with cv_real and dPdT) the general form of the same
+    identity, grad s = (c_v(rho, T)/T) grad T - (dP/dT)_rho / rho^2 grad rho."""
     gs = []
     for a in range(D):
         gT = 0.5 * (_shift(T, a, 1, D, per[a]) - _shift(T, a, -1, D, per[a]))
         gr = 0.5 * (_shift(rho, a, 1, D, per[a]) - _shift(rho, a, -1, D, per[a]))
-        gs.append(cv / T * gT - R / (rho * (1.0 - b * rho)) * gr)
+        if fluid is None:
+            gs.append(cv / T * gT - R / (rho * (1.0 - b * rho)) * gr)
+        else:
+            gs.append(fluid.cv_real(rho, T) / T * gT - fluid.dPdT(rho, T) / (rho * rho) * gr)
     return np.sqrt(sum(x * x for x in gs))
 
 
@@ -244,12 +250,12 @@ def binomial_filter(f, D, per):
     return f
 
 
-def numerical_transport(rho, u, T, cs2, coef, b, R, cv, D, per):
+def numerical_transport(rho, u, T, cs2, coef, b, R, cv, D, per, fluid=None):
     """(mu, eta, k)^num = (rho C_mu F4(S), rho C_eta F4(S), rho c_s C_k F4(|grad s|)),
     F4 = filtered fourth-difference norm; c_s = sqrt(max(c_s^2, 0))."""
     C_mu, C_eta, C_k = coef
     s4 = binomial_filter(fourth_difference_norm(strain_rate_magnitude(u, D, per), D, per), D, per)
-    g4 = binomial_filter(fourth_difference_norm(entropy_gradient_magnitude(rho, T, b, R, cv, D, per), D, per),
+    g4 = binomial_filter(fourth_difference_norm(entropy_gradient_magnitude(rho, T, b, R, cv, D, per, fluid), D, per),
                          D, per)
     return rho * C_mu * s4, rho * C_eta * s4, rho * np.sqrt(np.maximum(cs2, 0.0)) * C_k * g4
 
@@ -257,7 +263,12 @@ def numerical_transport(rho, u, T, cs2, coef, b, R, cv, D, per):
 class Model:
     """Constants of one run: lattice, vdW parameters, transport and boundaries.
 
-    eos: dict with a, b, R (lattice units), kappa, eta_over_mu, rho_ref, T_ref.
+    eos: dict with a, b, R (lattice units), kappa, eta_over_mu, rho_ref, T_ref, and
+    optionally kind = "pr" with Tc and m: the Peng-Robinson fluid of oracle/eos.py
+    (T_c and the slope m of sqrt(alpha)), whose temperature comes from its
+    non-linear caloric relation (Sec. 2, closing remark on Eq. lbm_temp).  Its exact
+    closure runs through the closure hook, and its sound speed and entropy
+    gradient enter the shock capturing.
     x_low / x_high: "periodic", "outflow", ("inflow", (rho, u_vector, T)) or
     ("wall", (u_vector, T)): a wall moving with velocity u at temperature T
     (the thermal Couette flow of Sec. 4.1; the paper gives no wall scheme).
@@ -285,15 +296,23 @@ class Model:
         self.kappa = float(eos["kappa"])
         self.eta_over_mu = float(eos["eta_over_mu"])
         rho_ref, T_ref = float(eos["rho_ref"]), float(eos["T_ref"])
+        self.fluid = None
+        if eos.get("kind", "vdw") == "pr":
+            self.fluid = eos_pr.PengRobinson(self.a, self.b, self.R, self.cv, float(eos["Tc"]), float(eos["m"]))
+            P_ref, cp_ref = self.fluid.pressure(rho_ref, T_ref), self.fluid.cp(rho_ref, T_ref)
+        else:
+            P_ref = thermo.pressure(rho_ref, T_ref, self.a, self.b, self.R)
+            cp_ref = thermo.cp(rho_ref, T_ref, self.a, self.b, self.R, self.cv)
         # tau = mu/P (Sec. 3.1): the given tau fixes the constant mu at the reference state
-        self.mu = float(tau) * thermo.pressure(rho_ref, T_ref, self.a, self.b, self.R)
+        self.mu = float(tau) * P_ref
         # Eq. qc: k/mu from the Prandtl number Pr = mu c_p / k at the reference state
-        self.k_over_mu = thermo.cp(rho_ref, T_ref, self.a, self.b, self.R, self.cv) / float(Pr)
+        self.k_over_mu = cp_ref / float(Pr)
         self.x_low, self.x_high = x_low, x_high
         # Optional thermodynamic closure (rho, e) -> (T, P, c_s^2) standing in
         # for Eqs. lbm_temp, Pvdw and vdW_speed_of_sound (a learned closure);
-        # None: the exact van der Waals relations.
-        self.closure = None
+        # None: the exact van der Waals relations.  A Peng-Robinson fluid starts
+        # with its exact closure (the Newton inversion of its caloric relation).
+        self.closure = None if self.fluid is None else self.fluid.closure
         # Optional shock capturing (C_mu, C_eta, C_k) of Sec. 4.4: numerical
         # transport coefficients added to mu, eta, k; those of step t come from
         # the primitive fields of step t-1 (zero at the first step).  None: off.
@@ -322,9 +341,12 @@ class Model:
 
     def state_eq(self, rho, u, T):
         """(f^eq, g^eq) at a primitive state (Fig. FlowChart, Initialize)."""
-        P = thermo.pressure(rho, T, self.a, self.b, self.R)
+        if self.fluid is None:
+            P = thermo.pressure(rho, T, self.a, self.b, self.R)
+            e = thermo.internal_energy(rho, T, self.a, self.cv)
+        else:
+            P, e = self.fluid.pressure(rho, T), self.fluid.energy(rho, T)
         theta = P / rho                                   # Eq. theta
-        e = thermo.internal_energy(rho, T, self.a, self.cv)
         zeta = [theta + ua * ua for ua in u]              # Eq. def_zeta_eq
         return (f_equilibrium(rho, u, zeta, self.c),
                 g_equilibrium(rho, u, theta, e, self.c))
@@ -454,9 +476,12 @@ class Sim:
             k_over_mu = k_e / mu_e
             per = [m.periodic_x] + [True] * (D - 1)
             # c_s of k^num: the van der Waals sound speed at (rho, T), whatever the closure
-            cs2_vdw = thermo.sound_speed_sq(rho[I], T[I], m.a, m.b, m.R, m.cv)
+            if m.fluid is None:
+                cs2_vdw = thermo.sound_speed_sq(rho[I], T[I], m.a, m.b, m.R, m.cv)
+            else:
+                cs2_vdw = m.fluid.sound_speed_sq(rho[I], T[I])
             self.visc = numerical_transport(rho[I], [ua[I] for ua in u], T[I], cs2_vdw, m.shock_capturing,
-                                            m.b, m.R, m.cv, D, per)
+                                            m.b, m.R, m.cv, D, per, m.fluid)
         beta = 1.0 / (2.0 * tau + 1.0)                                 # Eq. beta_main
 
         # step 4: derivatives (central; upwind for Phi)

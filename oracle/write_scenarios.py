@@ -163,6 +163,36 @@ def tgv(N=256, nu_reduced=1e-3):
                 Re=0.5 * math.sqrt(thermo.sound_speed_sq(rho0, T0, A_R, B, R_GAS, CV)) / nu_reduced)
 
 
+def tgv_pr(N=256, nu_reduced=1e-3, omega=0.0372):
+    """The compressible Taylor-Green vortex of tgv() in a Peng-Robinson fluid (the
+    general-EOS case of Sec. 2: temperature from a non-linear caloric relation).
+
+    Reduced units with the critical point at rho = T = P = 1 (oracle/eos.py,
+    Z_c = 0.3074); acentric factor omega (nitrogen's), c_v = 2.5 R (a diatomic
+    ideal part).  Same state (rho0 0.6, T0 1.05), Mach number 0.5, Re and velocity
+    rule (theta / U^2 <= 1/4) as tgv(); Stokes hypothesis (eta/mu = 0).  The
+    temperature field gives the classical TGV pressure at constant density to first
+    order: T = T0 + dP / (dP/dT)_rho, T_amp = rho0 U0^2 / (16 (dP/dT)_rho)."""
+    from . import eos as eos_pr
+    a_r, b_r, R_r = eos_pr.reduced_constants()
+    m = eos_pr.m_of_omega(omega)
+    cv = 2.5 * R_r
+    pr = eos_pr.PengRobinson(a_r, b_r, R_r, cv, 1.0, m)
+    rho0, T0 = 0.6, 1.05
+    U2 = float(math.ceil(pr.pressure(rho0, T0) / rho0 / 0.25))
+    eos = dict(kind="pr", a=a_r / U2, b=b_r, R=R_r, Tc=1.0 / U2, m=m, kappa=0.01, eta_over_mu=0.0,
+               rho_ref=rho0, T_ref=T0 / U2)
+    prl = eos_pr.PengRobinson(eos["a"], b_r, R_r, cv, eos["Tc"], m)
+    cs = math.sqrt(prl.sound_speed_sq(rho0, T0 / U2))
+    U0 = 0.5 * cs
+    T_amp = rho0 * U0 * U0 / (16.0 * prl.dPdT(rho0, T0 / U2))
+    nu_lat = nu_reduced / (math.sqrt(U2) * 2.0 * math.pi / N)
+    tau = nu_lat * rho0 / prl.pressure(rho0, T0 / U2)
+    return dict(D=3, U2=U2, cv=cv, Pr=0.71, nu_reduced=nu_reduced, N=N, nu=nu_lat, eos=eos, tau=tau, rho0=rho0,
+                T0=T0 / U2, U0=U0, T_amp=T_amp, cs=cs, omega=omega,
+                crit=dict(a=a_r, b=b_r, R=R_r))
+
+
 def strong_shock(D, Ma=1.47, nu=0.01):
     """Planar Ma 1.47 shock into the supercritical vapour (rho 0.3, T 1.1), no drop.
 
@@ -283,6 +313,7 @@ def main():
         shock_drop_d3q27=_shock_drop(3, 1.47, 0.01),
         strong_shock_d2q9=strong_shock(2),
         strong_shock_d3q27=strong_shock(3),
+        tgv_pr_d3q27=tgv_pr(),
         column_d2q9=shock_column(2),
         column_d3q27=shock_column(3),
         couette_d2q9=couette(2),

@@ -154,3 +154,13 @@ def test_korteweg_force_without_density_breaks_coexistence_pin(monkeypatch):
     import pytest as _pytest
     with _pytest.raises(AssertionError):
         tc.test_slab_plateaus_reach_maxwell_coexistence()
+
+
+def test_departure_energy_without_alpha_slope_breaks_caloric_pin(monkeypatch):
+    """e - c_v T = -(a alpha - T a alpha') L / (2 sqrt2 b): dropping T a alpha' is caught."""
+    import test_oracle_pr as tp
+    from oracle import eos as oeos
+    monkeypatch.setattr(oeos.PengRobinson, "energy_departure",
+                        lambda self, rho, T: -self.a * self.alpha(T) * self._L(rho) / (2.0 * oeos.SQRT2 * self.b))
+    with pytest.raises(AssertionError):
+        tp.test_caloric_relation_against_quadrature(0.6, 1.05)
