@@ -34,6 +34,9 @@ WORKLOADS = {
     "tgv256": ("tgv", dict(N=256), "fp32", "D3Q27 compressible Taylor-Green vortex 256^3, vdW dense vapour, FP32"),
     "tgv128": ("tgv", dict(N=128), "fp32", "D3Q27 Taylor-Green 128^3, FP32 (small profiling case)"),
     "tgv256-fp64": ("tgv", dict(N=256), "fp64", "D3Q27 compressible Taylor-Green vortex 256^3, FP64"),
+    "tgv256-pr": ("tgv", dict(N=256, scenario_name="tgv_pr_d3q27"), "fp32",
+                  "D3Q27 compressible Taylor-Green vortex 256^3 in a Peng-Robinson fluid (nitrogen-like; temperature "
+                  "from the caloric relation, inverted per node in FP64), FP32"),
     "tgv256-fp16dev": ("tgv", dict(N=256), "fp16dev", "D3Q27 Taylor-Green 256^3, FP16-deviation storage"),
     "riemann": ("riemann", dict(), "fp64", "D2Q9 non-ideal Riemann problem 1000x4, FP64"),
     "shockdrop2d": ("shock_column", dict(D=2, shape=(4096, 2048), radius=128), "fp32",
@@ -219,8 +222,9 @@ def _oracle_sample(workload, seconds, steps=None, warmup=1):
     from oracle import lbm as olbm
     builder, kw, prec, _ = WORKLOADS[workload]
     if builder == "tgv":
-        case = inputs.tgv(shape=(48, 48, 48))
-        sample = "D3Q27 Taylor-Green 48^3 box (same state, k scaled), FP64 oracle"
+        case = inputs.tgv(shape=(48, 48, 48), scenario_name=kw.get("scenario_name", "tgv_d3q27"))
+        sample = "D3Q27 Taylor-Green 48^3 box (same state, k scaled%s), FP64 oracle" % (
+            ", Peng-Robinson fluid, Newton temperature" if "scenario_name" in kw else "")
     elif builder == "riemann":
         case = inputs.riemann()
         sample = "D2Q9 Riemann 1000x4 (the full workload), FP64 oracle"

@@ -83,23 +83,39 @@ enum {
   LBM_FLAG_PRESSURE = 8u     /* warning: P <= 0                                */
 };
 
-/* van der Waals fluid and model parameters, lattice units.
+/* equations of state (lbm_eos.kind) */
+enum { LBM_EOS_VDW = 0, LBM_EOS_PR = 1 };
+
+/* Fluid and model parameters, lattice units.
+ * kind LBM_EOS_VDW, the van der Waals fluid of the paper:
  *   P = rho R T / (1 - b rho) - a rho^2               (Eq. Pvdw)
  *   e = c_v T - a rho                                 (Eq. de_vdW)
+ * kind LBM_EOS_PR, the Peng-Robinson fluid (the general equation of state of
+ * Sec. 2, whose temperature needs a non-linear caloric inversion):
+ *   P = rho R T / (1 - b rho) - a alpha(T) rho^2 / (1 + 2 b rho - b^2 rho^2),
+ *   alpha = (1 + m (1 - sqrt(T / Tc)))^2,
+ *   e = c_v T + (T a alpha' - a alpha) L(rho) / (2 sqrt2 b),
+ *   L = ln((1 + (1 + sqrt2) b rho) / (1 + (1 - sqrt2) b rho))
+ * (the identity e = c_v T + int_0^rho (P - T dP/dT)/rho'^2 drho', c_v the
+ * ideal-gas part); T(rho, e) is the positive root of a quadratic in sqrt(T),
+ * taken in FP64 in every precision.  Peng-Robinson handles step with the exact
+ * closure in FP32 or FP64 (fused or multipass); FP16-deviation storage, the
+ * learned closure and batches are van der Waals only.
  * kappa: Korteweg capillarity coefficient, F = kappa rho grad lap rho (Eq. FK).
  * eta_over_mu: bulk to shear viscosity ratio entering alpha (Eq. corr_bulk).
  * rho_ref, T_ref: reference state fixing the constant mu = tau P(rho_ref, T_ref)
  *   and k = mu c_p(rho_ref, T_ref) / Pr; for LBM_FP16DEV also the state whose
  *   equilibria are subtracted before storage.
- * kind must be 0 (van der Waals). */
+ * Tc, m: Peng-Robinson only (Tc > 0, m >= 0). */
 typedef struct {
-  int kind;
+  int kind;            /* LBM_EOS_VDW | LBM_EOS_PR */
   double a, b, R;
   double kappa;
   double eta_over_mu;
   double rho_ref, T_ref;
   int precision;       /* LBM_FP64 | LBM_FP32 | LBM_FP16DEV */
   int closure;         /* LBM_CLOSURE_EXACT | LBM_CLOSURE_MLP */
+  double Tc, m;        /* Peng-Robinson critical temperature and alpha slope */
 } lbm_eos;
 
 /* Create a solver of Nx*Ny*Nz interior nodes (Nz = 1 for D2Q9).

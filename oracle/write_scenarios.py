@@ -169,8 +169,10 @@ def tgv_pr(N=256, nu_reduced=1e-3, omega=0.0372):
 
     Reduced units with the critical point at rho = T = P = 1 (oracle/eos.py,
     Z_c = 0.3074); acentric factor omega (nitrogen's), c_v = 2.5 R (a diatomic
-    ideal part).  Same state (rho0 0.6, T0 1.05), Mach number 0.5, Re and velocity
-    rule (theta / U^2 <= 1/4) as tgv(); Stokes hypothesis (eta/mu = 0).  The
+    ideal part).  Same state (rho0 0.6, T0 1.05), Mach number 0.5 and Re as tgv();
+    Stokes hypothesis (eta/mu = 0).  Velocity scale: this fluid's sound speed is
+    larger against theta than the van der Waals one's, so the rule of strong_shock
+    sets U^2: (theta + U0^2) / U^2 <= 0.27 and theta / U^2 <= 1/4.  The
     temperature field gives the classical TGV pressure at constant density to first
     order: T = T0 + dP / (dP/dT)_rho, T_amp = rho0 U0^2 / (16 (dP/dT)_rho)."""
     from . import eos as eos_pr
@@ -179,7 +181,8 @@ def tgv_pr(N=256, nu_reduced=1e-3, omega=0.0372):
     cv = 2.5 * R_r
     pr = eos_pr.PengRobinson(a_r, b_r, R_r, cv, 1.0, m)
     rho0, T0 = 0.6, 1.05
-    U2 = float(math.ceil(pr.pressure(rho0, T0) / rho0 / 0.25))
+    th_r, U0_r = pr.pressure(rho0, T0) / rho0, 0.5 * math.sqrt(pr.sound_speed_sq(rho0, T0))
+    U2 = float(max(math.ceil(th_r / 0.25), math.ceil((th_r + U0_r * U0_r) / 0.27)))
     eos = dict(kind="pr", a=a_r / U2, b=b_r, R=R_r, Tc=1.0 / U2, m=m, kappa=0.01, eta_over_mu=0.0,
                rho_ref=rho0, T_ref=T0 / U2)
     prl = eos_pr.PengRobinson(eos["a"], b_r, R_r, cv, eos["Tc"], m)

@@ -22,6 +22,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2
 LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
 LBM_CLOSURE_EXACT, LBM_CLOSURE_MLP = 0, 1
 LBM_BC_PERIODIC, LBM_BC_OUTFLOW, LBM_BC_INFLOW, LBM_BC_WALL = 0, 1, 2, 3
+LBM_EOS_VDW, LBM_EOS_PR = 0, 1
 LBM_FACE_XLO, LBM_FACE_XHI = 0, 1
 LBM_FLAG_NONFINITE, LBM_FLAG_NEGATIVE, LBM_FLAG_THETA, LBM_FLAG_PRESSURE = 1, 2, 4, 8
 LBM_STEP_FUSED, LBM_STEP_MULTIPASS = 0, 1
@@ -58,7 +59,8 @@ class lbm_eos(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
                 ("R", ctypes.c_double), ("kappa", ctypes.c_double), ("eta_over_mu", ctypes.c_double),
                 ("rho_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
-                ("precision", ctypes.c_int), ("closure", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("closure", ctypes.c_int),
+                ("Tc", ctypes.c_double), ("m", ctypes.c_double)]
 
 
 _lib = None
@@ -165,9 +167,11 @@ def _dptr(t):
 
 def lbm_create(lattice, Nx, Ny, Nz, eos, tau, Pr, cv, precision="fp64", closure=LBM_CLOSURE_EXACT):
     lib = load()
-    e = lbm_eos(kind=0, a=eos["a"], b=eos["b"], R=eos["R"], kappa=eos["kappa"],
+    pr = eos.get("kind", "vdw") == "pr"
+    e = lbm_eos(kind=LBM_EOS_PR if pr else LBM_EOS_VDW, a=eos["a"], b=eos["b"], R=eos["R"], kappa=eos["kappa"],
                 eta_over_mu=eos["eta_over_mu"], rho_ref=eos["rho_ref"], T_ref=eos["T_ref"],
-                precision=PRECISIONS.get(precision, precision), closure=closure)
+                precision=PRECISIONS.get(precision, precision), closure=closure,
+                Tc=eos["Tc"] if pr else 0.0, m=eos["m"] if pr else 0.0)
     h = ctypes.c_void_p()
     _check(lib.lbm_create(ctypes.byref(h), lattice, Nx, Ny, Nz, ctypes.byref(e), tau, Pr, cv))
     return h
@@ -333,7 +337,8 @@ class Batch:
         Ny = (ctypes.c_int * n)(*[c.shape[1] for c in cases])
         Nz = (ctypes.c_int * n)(*[(c.shape[2] if c.D == 3 else 1) for c in cases])
         e = c0.eos
-        eos = lbm_eos(kind=0, a=e["a"], b=e["b"], R=e["R"], kappa=e["kappa"], eta_over_mu=e["eta_over_mu"],
+        eos = lbm_eos(kind=LBM_EOS_PR if e.get("kind", "vdw") == "pr" else LBM_EOS_VDW, a=e["a"], b=e["b"], R=e["R"],
+                      kappa=e["kappa"], eta_over_mu=e["eta_over_mu"],
                       rho_ref=e["rho_ref"], T_ref=e["T_ref"], precision=PRECISIONS.get(precision, precision),
                       closure=LBM_CLOSURE_EXACT)
         self.b = ctypes.c_void_p()

@@ -1,0 +1,18 @@
+// Fused step with the exact Peng-Robinson closure: D = 3, FP32 and FP64 storage
+// and arithmetic (the temperature inversion in FP64 in both).
+#include "lbm_ops.cuh"
+
+namespace lbm {
+void step_d3_fp32_pr(Handle& h, const void* src, void* dst) {
+  OpsImpl<3, float, float>::step_cl<PrClosure<float>>(h, src, dst);
+}
+int autotune_d3_fp32_pr(Handle& h, int reps, float* best_ms) {
+  return OpsImpl<3, float, float>::autotune_cl<PrClosure<float>>(h, reps, best_ms);
+}
+void step_d3_fp64_pr(Handle& h, const void* src, void* dst) {
+  OpsImpl<3, double, double>::step_cl<PrClosure<double>>(h, src, dst);
+}
+int autotune_d3_fp64_pr(Handle& h, int reps, float* best_ms) {
+  return OpsImpl<3, double, double>::autotune_cl<PrClosure<double>>(h, reps, best_ms);
+}
+}  // namespace lbm

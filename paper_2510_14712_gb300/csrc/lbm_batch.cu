@@ -91,6 +91,7 @@ int lbm_batch_create(lbm_batch_t* out, int lattice, int n, const int* Nx, const 
   if (n < 1) return bfail(LBM_EINVAL, "n must be >= 1");
   if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return bfail(LBM_EINVAL, "lattice must be 9 or 27");
   if (lattice == LBM_D3Q27 && !Nz) return bfail(LBM_EINVAL, "D3Q27 batches need Nz");
+  if (eos->kind != LBM_EOS_VDW) return bfail(LBM_EINVAL, "batches use the van der Waals fluid");
   lbm_batch_s* b = new (std::nothrow) lbm_batch_s();
   if (!b) return bfail(LBM_ENOMEM, "host allocation failed");
   std::memset(static_cast<Batch*>(b), 0, sizeof(Batch));

@@ -54,7 +54,27 @@ Ops with_mlp(const Ops* base, void (*step)(Handle&, const void*, void*), int (*t
   return o;
 }
 
+// Exact-closure table with the fused step and the autotuner of the Peng-Robinson
+// closure (the multi-pass step is EOS-generic; batches are van der Waals only).
+Ops with_pr(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*)) {
+  Ops o = *base;
+  o.step = step;
+  o.autotune = tune;
+  o.batch_ncfg = nullptr;
+  o.batch_prepare = nullptr;
+  o.batch_enqueue = nullptr;
+  return o;
+}
+
 const Ops* ops_for(const Handle& h) {
+  if (h.p.eos_kind == LBM_EOS_PR) {
+    static const Ops p2f = with_pr(ops_d2_fp32(), step_d2_fp32_pr, autotune_d2_fp32_pr);
+    static const Ops p3f = with_pr(ops_d3_fp32(), step_d3_fp32_pr, autotune_d3_fp32_pr);
+    static const Ops p2d = with_pr(ops_d2_fp64(), step_d2_fp64_pr, autotune_d2_fp64_pr);
+    static const Ops p3d = with_pr(ops_d3_fp64(), step_d3_fp64_pr, autotune_d3_fp64_pr);
+    if (h.precision == LBM_FP64) return h.D == 2 ? &p2d : &p3d;
+    return h.D == 2 ? &p2f : &p3f;
+  }
   if (h.closure == LBM_CLOSURE_MLP) {
     static const Ops m2 = with_mlp(ops_d2_fp32(), step_d2_fp32_mlp, autotune_d2_fp32_mlp);
     static const Ops m3 = with_mlp(ops_d3_fp32(), step_d3_fp32_mlp, autotune_d3_fp32_mlp);
@@ -241,7 +261,12 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
   if (Nx < 1 || Ny < 1 || Nz < 1) return fail(LBM_EINVAL, "sizes must be >= 1");
   if (D == 2 && Nz != 1) return fail(LBM_EINVAL, "D2Q9 needs Nz == 1");
   if (!(tau > 0) || !(Pr > 0) || !(cv > 0)) return fail(LBM_EINVAL, "tau, Pr, cv must be > 0");
-  if (eos->kind != 0) return fail(LBM_EINVAL, "only the van der Waals EOS (kind 0) is supported");
+  if (eos->kind != LBM_EOS_VDW && eos->kind != LBM_EOS_PR) return fail(LBM_EINVAL, "unknown equation of state");
+  if (eos->kind == LBM_EOS_PR) {
+    if (!(eos->Tc > 0) || !(eos->m >= 0) || !std::isfinite(eos->m))
+      return fail(LBM_EINVAL, "Peng-Robinson needs Tc > 0 and a finite m >= 0");
+    if (eos->precision == LBM_FP16DEV) return fail(LBM_EINVAL, "Peng-Robinson handles use FP32 or FP64 storage");
+  }
   if (!(eos->rho_ref > 0) || !(eos->T_ref > 0) || !(eos->b * eos->rho_ref < 1) || !(eos->R > 0))
     return fail(LBM_EINVAL, "need rho_ref > 0, T_ref > 0, R > 0, b rho_ref < 1");
   if (eos->precision < LBM_FP64 || eos->precision > LBM_FP16DEV) return fail(LBM_EINVAL, "bad precision");
@@ -266,15 +291,24 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
   p.bc_lo = p.bc_hi = LBM_BC_PERIODIC;
   p.a = eos->a; p.b = eos->b; p.R = eos->R; p.cv = cv;
   p.kappa = eos->kappa; p.eta_over_mu = eos->eta_over_mu;
+  p.eos_kind = eos->kind;
+  p.Tc = eos->kind == LBM_EOS_PR ? eos->Tc : 0.0;
+  p.mpr = eos->kind == LBM_EOS_PR ? eos->m : 0.0;
   Model<double> m = host_model(*h);
-  const double P_ref = vdw_pressure(m, eos->rho_ref, eos->T_ref);
+  const double P_ref = eos_pressure(m, eos->rho_ref, eos->T_ref);
   if (!(P_ref > 0)) {
     delete h;
     return fail(LBM_EINVAL, "P(rho_ref, T_ref) must be > 0");
   }
   p.mu = tau * P_ref;                                      // tau = mu / P at the reference state
   const double RT = eos->R * eos->T_ref, x = 1.0 - eos->b * eos->rho_ref;
-  const double cp = cv + eos->R * eos->R * eos->T_ref / (RT - 2.0 * eos->a * eos->rho_ref * x * x);  // Eq. cpvdW
+  double cp = cv + eos->R * eos->R * eos->T_ref / (RT - 2.0 * eos->a * eos->rho_ref * x * x);  // Eq. cpvdW
+  if (eos->kind == LBM_EOS_PR) {   // c_p = c_v(rho, T) + T (dP/dT)^2 / (rho^2 dP/drho)
+    const double r = eos->rho_ref, T = eos->T_ref, dPdT = pr_dPdT(m, r, T);
+    const double cs2 = pr_cs2(m, r, T), cvr = pr_cv(m, r, T);
+    const double dPdr = cs2 - T * dPdT * dPdT / (r * r * cvr);
+    cp = cvr + T * dPdT * dPdT / (r * r * dPdr);
+  }
   p.k_over_mu = cp / Pr;                                   // Pr = mu c_p / k
   m = host_model(*h);
   if (h->precision == LBM_FP16DEV) {

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/lbm.h"
+
 namespace lbm {
 
 // Velocity i <-> (c_x, c_y[, c_z]) in {-1,0,1}^D, lexicographic with the last
@@ -46,11 +48,13 @@ template <int D, typename real> __device__ __forceinline__ void first_moment(con
 
 // Model constants in the arithmetic type.
 template <typename real> struct Model {
-  real a, b, R, cv;          // van der Waals (Eq. Pvdw), c_v
+  real a, b, R, cv;          // van der Waals (Eq. Pvdw) or Peng-Robinson constants, c_v (ideal part)
   real kappa;                // Korteweg capillarity (Eq. FK)
   real eta_over_mu;          // bulk / shear viscosity (Eq. corr_bulk)
   real mu;                   // shear viscosity (constant, Sec. 2)
   real k_over_mu;            // thermal conductivity / mu (Eq. qc)
+  int kind;                  // LBM_EOS_VDW or LBM_EOS_PR
+  real Tc, mpr;              // Peng-Robinson: T_c and the slope m of sqrt(alpha) in sqrt(T/T_c)
 };
 
 template <typename real> __host__ __device__ inline real vdw_pressure(const Model<real>& m, real rho, real T) {
@@ -62,6 +66,82 @@ template <typename real> __host__ __device__ inline real vdw_energy(const Model<
 template <typename real> __host__ __device__ inline real vdw_cs2(const Model<real>& m, real rho, real T) {
   const real s = real(1) / (real(1) - m.b * rho);
   return m.R * T * (real(1) + m.R / m.cv) * s * s - real(2) * m.a * rho;   // Eq. vdW_speed_of_sound
+}
+
+// ---- Peng-Robinson fluid (a general equation of state, Sec. 2) ----
+//   P = rho R T / (1 - b rho) - a alpha(T) rho^2 / D(rho),  D = 1 + 2 b rho - b^2 rho^2,
+//   alpha = s^2,  s = 1 + m (1 - sqrt(T / T_c)),
+// with the caloric relation of the identity e = c_v T + int_0^rho (P - T dP/dT) / rho'^2:
+//   e = c_v T + (T a alpha' - a alpha) L(rho) / (2 sqrt2 b),  L = ln((1 + (1+sqrt2) b rho) / (1 + (1-sqrt2) b rho)).
+// Since T alpha' - alpha = -(1 + m) s, e = c_v T + A sqrt(T) + B0 with
+//   A = a c (1 + m) m / sqrt(T_c),  B0 = -a c (1 + m)^2,  c = L / (2 sqrt2 b):
+// a quadratic in sqrt(T), inverted below in closed form.
+template <typename real> __host__ __device__ inline real pr_c(const Model<real>& m, real rho) {
+  const real r2 = real(1.4142135623730951);
+  return log((real(1) + (real(1) + r2) * m.b * rho) / (real(1) + (real(1) - r2) * m.b * rho)) / (real(2) * r2 * m.b);
+}
+template <typename real> __host__ __device__ inline real pr_s(const Model<real>& m, real T) {
+  return real(1) + m.mpr * (real(1) - sqrt(T / m.Tc));
+}
+template <typename real> __host__ __device__ inline real pr_pressure(const Model<real>& m, real rho, real T) {
+  const real s = pr_s(m, T), D = real(1) + real(2) * m.b * rho - m.b * m.b * rho * rho;
+  return rho * m.R * T / (real(1) - m.b * rho) - m.a * s * s * rho * rho / D;
+}
+template <typename real> __host__ __device__ inline real pr_energy(const Model<real>& m, real rho, real T) {
+  return m.cv * T - m.a * pr_c(m, rho) * (real(1) + m.mpr) * pr_s(m, T);
+}
+// (dP/dT)_rho, (dP/drho)_T, c_v(rho, T) and Eq. speed_of_sound
+template <typename real> __host__ __device__ inline real pr_dPdT(const Model<real>& m, real rho, real T) {
+  const real s = pr_s(m, T), D = real(1) + real(2) * m.b * rho - m.b * m.b * rho * rho;
+  const real dal = -m.mpr * s / sqrt(T * m.Tc);
+  return rho * m.R / (real(1) - m.b * rho) - m.a * dal * rho * rho / D;
+}
+template <typename real> __host__ __device__ inline real pr_cv(const Model<real>& m, real rho, real T) {
+  const real s = pr_s(m, T);
+  const real d2al = real(0.5) * m.mpr / T * (m.mpr / m.Tc + s / sqrt(T * m.Tc));
+  return m.cv + T * m.a * d2al * pr_c(m, rho);
+}
+template <typename real> __host__ __device__ inline real pr_cs2(const Model<real>& m, real rho, real T) {
+  const real s = pr_s(m, T), D = real(1) + real(2) * m.b * rho - m.b * m.b * rho * rho;
+  const real x = real(1) - m.b * rho;
+  const real dPdr = m.R * T / (x * x) - m.a * s * s * real(2) * rho * (real(1) + m.b * rho) / (D * D);
+  const real dPdT = pr_dPdT(m, rho, T);
+  return dPdr + T * dPdT * dPdT / (rho * rho * pr_cv(m, rho, T));
+}
+// T from (rho, e): the positive root of c_v y^2 + A y + (B0 - e) = 0, y = sqrt(T), in
+// FP64 and in the form without cancellation, y = 2 (e - B0) / (A + sqrt(A^2 + 4 c_v (e - B0)))
+template <typename real> __host__ __device__ inline double pr_temperature(const Model<real>& m, real rho, real e) {
+  const double c = double(pr_c(m, rho)), a = m.a, k = m.mpr, cv = m.cv;
+  const double A = a * c * (1.0 + k) * k / sqrt(double(m.Tc)), B0 = -a * c * (1.0 + k) * (1.0 + k);
+  const double q = double(e) - B0;
+  const double y = 2.0 * q / (A + sqrt(A * A + 4.0 * cv * q));
+  return y * y;
+}
+
+// ---- the fluid of a handle (Model::kind): van der Waals or Peng-Robinson ----
+template <typename real> __host__ __device__ inline real eos_pressure(const Model<real>& m, real rho, real T) {
+  return m.kind == LBM_EOS_PR ? pr_pressure(m, rho, T) : vdw_pressure(m, rho, T);
+}
+template <typename real> __host__ __device__ inline real eos_energy(const Model<real>& m, real rho, real T) {
+  return m.kind == LBM_EOS_PR ? pr_energy(m, rho, T) : vdw_energy(m, rho, T);
+}
+template <typename real> __host__ __device__ inline real eos_cs2(const Model<real>& m, real rho, real T) {
+  return m.kind == LBM_EOS_PR ? pr_cs2(m, rho, T) : vdw_cs2(m, rho, T);
+}
+// T from rho and the specific internal energy e (Eq. lbm_temp for van der Waals)
+template <typename real> __host__ __device__ inline real eos_temperature(const Model<real>& m, real rho, real e) {
+  return m.kind == LBM_EOS_PR ? real(pr_temperature(m, rho, e)) : (e + m.a * rho) / m.cv;
+}
+// the coefficients of grad s = c_T grad T - c_rho grad rho: c_v(rho, T)/T and (dP/dT)_rho / rho^2
+template <typename real>
+__host__ __device__ inline void eos_entropy_coefs(const Model<real>& m, real rho, real T, real& cT, real& cR) {
+  if (m.kind == LBM_EOS_PR) {
+    cT = pr_cv(m, rho, T) / T;
+    cR = pr_dPdT(m, rho, T) / (rho * rho);
+  } else {
+    cR = m.R / (rho * (real(1) - m.b * rho));
+    cT = m.cv / T;
+  }
 }
 
 // Eq. phi: Psi(c; xi, zeta) = 1 - zeta (c = 0), (zeta + c xi)/2 (c = +-1).
@@ -99,9 +179,9 @@ template <typename real> __host__ __device__ inline Axis3<real> chi3(real u, rea
 template <int D, typename real>
 __host__ __device__ inline void equilibria(const Model<real>& m, real rho, const real* u, real T, real* feq, real* geq) {
   using L = Lattice<D>;
-  const real P = vdw_pressure(m, rho, T);
+  const real P = eos_pressure(m, rho, T);
   const real theta = P / rho;
-  const real e = vdw_energy(m, rho, T);
+  const real e = eos_energy(m, rho, T);
   Axis3<real> ps[D], ch[D];
   for (int a = 0; a < D; ++a) {
     ps[a] = psi3(u[a], theta + u[a] * u[a]);

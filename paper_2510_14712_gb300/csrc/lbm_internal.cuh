@@ -25,6 +25,8 @@ struct Params {
   int bc_lo, bc_hi;           // LBM_BC_* of the x faces
   // model (FP64 master copy)
   double a, b, R, cv, kappa, eta_over_mu, mu, k_over_mu;
+  int eos_kind;               // LBM_EOS_VDW | LBM_EOS_PR
+  double Tc, mpr;             // Peng-Robinson T_c and alpha slope
   // inflow states (rho, u[3], T) and their equilibria (post-collision ghosts);
   // wall faces: (unused, u[3], T) of the wall
   double st_lo[5], st_hi[5];
@@ -48,6 +50,7 @@ template <typename real> __host__ __device__ inline Model<real> model_of(const P
   m.a = real(p.a); m.b = real(p.b); m.R = real(p.R); m.cv = real(p.cv);
   m.kappa = real(p.kappa); m.eta_over_mu = real(p.eta_over_mu);
   m.mu = real(p.mu); m.k_over_mu = real(p.k_over_mu);
+  m.kind = p.eos_kind; m.Tc = real(p.Tc); m.mpr = real(p.mpr);
   return m;
 }
 
@@ -145,6 +148,15 @@ const Ops* ops_d3_fp16();
 // fused step and tile autotuner with the learned closure (FP32 storage)
 void step_d2_fp32_mlp(Handle& h, const void* src, void* dst);
 void step_d3_fp32_mlp(Handle& h, const void* src, void* dst);
+// exact Peng-Robinson closure (lbm_eos.kind LBM_EOS_PR): fused step and its autotuner
+void step_d2_fp32_pr(Handle& h, const void* src, void* dst);
+void step_d3_fp32_pr(Handle& h, const void* src, void* dst);
+void step_d2_fp64_pr(Handle& h, const void* src, void* dst);
+void step_d3_fp64_pr(Handle& h, const void* src, void* dst);
+int autotune_d2_fp32_pr(Handle& h, int reps, float* best_ms);
+int autotune_d3_fp32_pr(Handle& h, int reps, float* best_ms);
+int autotune_d2_fp64_pr(Handle& h, int reps, float* best_ms);
+int autotune_d3_fp64_pr(Handle& h, int reps, float* best_ms);
 int autotune_d2_fp32_mlp(Handle& h, int reps, float* best_ms);
 int autotune_d3_fp32_mlp(Handle& h, int reps, float* best_ms);
 

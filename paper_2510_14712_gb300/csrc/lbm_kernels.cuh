@@ -257,10 +257,18 @@ __global__ void k_prims(Params p, const real* M, real* W) {
     u2 += u[a] * u[a];
   }
   const real E = (M[(1 + D) * p.plane + o] + real(0.5) * uF) / rho;                // Eq. def_E
-  const real T = (E - real(0.5) * u2 + m.a * rho) / m.cv;                            // Eq. lbm_temp
-  const real P = vdw_pressure(m, rho, T);
+  real T, P, h;
+  if (m.kind == LBM_EOS_PR) {   // the caloric relation inverted for T; h = e + P/rho
+    const real e = E - real(0.5) * u2;
+    T = eos_temperature(m, rho, e);
+    P = pr_pressure(m, rho, T);
+    h = e + P / rho;
+  } else {
+    T = (E - real(0.5) * u2 + m.a * rho) / m.cv;                                    // Eq. lbm_temp
+    P = vdw_pressure(m, rho, T);
+    h = vdw_energy(m, rho, T) + P / rho;                                             // Eq. enthalpy
+  }
   const real theta = P / rho;
-  const real h = vdw_energy(m, rho, T) + theta;                                      // Eq. enthalpy
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     W[a * p.plane + o] = u[a];
@@ -288,9 +296,9 @@ __global__ void k_collide(Params p, const typename Store<S>::T* A, typename Stor
   NodeState<D, real> s;
   s.rho = M[o];
   s.T = W[D * p.plane + o];
-  s.P = vdw_pressure(m, s.rho, s.T);
-  s.cs2 = vdw_cs2(m, s.rho, s.T);
-  s.e = vdw_energy(m, s.rho, s.T);
+  s.P = eos_pressure(m, s.rho, s.T);
+  s.cs2 = eos_cs2(m, s.rho, s.T);
+  s.e = eos_energy(m, s.rho, s.T);
   s.sc = p.sc_on != 0;
   s.mu_num = s.eta_num = s.k_num = real(0);
   if (s.sc) {

@@ -718,6 +718,7 @@ int lbm_mlp_attach(lbm_t h, lbm_mlp_t net) {
     return LBM_OK;
   }
   if (h->precision != LBM_FP32) return fail(LBM_EINVAL, "the learned closure needs FP32 population storage");
+  if (h->p.eos_kind != LBM_EOS_VDW) return fail(LBM_EINVAL, "the learned closure is trained on the van der Waals fluid");
   if (!net->scaled) return fail(LBM_ESTATE, "scaling not set (lbm_mlp_fit_scaling)");
   if (!h->mlp_img) CKM(cudaMalloc(&h->mlp_img, sizeof(Image)));
   // the network's stream finished its last update before its call returned

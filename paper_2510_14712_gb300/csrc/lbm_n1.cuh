@@ -72,7 +72,13 @@ __device__ __forceinline__ void n1_strain_at(const Params& p, const real* __rest
     for (int b = 0; b < D; ++b) acc += (g[a][b] + g[b][a]) * (g[a][b] + g[b][a]);
   out[o] = real(0.5) * sqrt(acc);
   const real r = rho[o], t = T[o];
-  const real cR = real(p.R) / (r * (real(1) - real(p.b) * r)), cT = real(p.cv) / t;
+  real cT, cR;
+  if (p.eos_kind == LBM_EOS_PR) {
+    eos_entropy_coefs(model_of<real>(p), r, t, cT, cR);
+  } else {
+    cR = real(p.R) / (r * (real(1) - real(p.b) * r));
+    cT = real(p.cv) / t;
+  }
   real gs2 = real(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -133,7 +139,7 @@ __device__ __forceinline__ void n1_filter_coef_at(const Params& p, const Model<r
                                                   real* __restrict__ visc, int x, int y, int z, unsigned o) {
   const real s4 = n1_binomial(p, in, 0, D - 1, x, y, z, o), g4 = n1_binomial(p, in, 1, D - 1, x, y, z, o);
   const real r = rho[o];
-  const real cs2 = vdw_cs2(m, r, T[o]);
+  const real cs2 = eos_cs2(m, r, T[o]);
   const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
   visc[o] = r * real(p.sc_c[0]) * s4;
   visc[p.plane + o] = r * real(p.sc_c[1]) * s4;

@@ -2,6 +2,8 @@
 // Each k_*.cu translation unit instantiates one of them.
 #pragma once
 
+#include <type_traits>
+
 #include <algorithm>
 #include <vector>
 
@@ -96,7 +98,12 @@ template <int D, typename S, typename real> struct OpsImpl {
   // The learned closure adds a register-hungry network evaluation to stage C,
   // so its list also offers the unrestricted (MINB 1) allocation.
   template <class CL> static int candidates(const LaunchFn** fns) {
-    if constexpr (D == 3) {
+    if constexpr (std::is_same<CL, PrClosure<real>>::value) {   // one shape: the Peng-Robinson sets compile fast
+      static const LaunchFn c[] = {D == 3 ? &Fused<32, 8, sizeof(real) == 8 ? 1 : 2, CL>::launch
+                                          : &Fused<256, 1, 2, CL>::launch};
+      *fns = c;
+      return 1;
+    } else if constexpr (D == 3) {
       if constexpr (sizeof(real) == 8) {
         static const LaunchFn c[] = {&Fused<32, 8, 1, CL>::launch};
         *fns = c;
