@@ -36,7 +36,7 @@ WORKLOADS = {
     "tgv256-fp64": ("tgv", dict(N=256), "fp64", "D3Q27 compressible Taylor-Green vortex 256^3, FP64"),
     "tgv256-pr": ("tgv", dict(N=256, scenario_name="tgv_pr_d3q27"), "fp32",
                   "D3Q27 compressible Taylor-Green vortex 256^3 in a Peng-Robinson fluid (nitrogen-like; temperature "
-                  "from the caloric relation, inverted per node in FP64), FP32"),
+                  "from the caloric relation, inverted per node), FP32"),
     "tgv256-fp16dev": ("tgv", dict(N=256), "fp16dev", "D3Q27 Taylor-Green 256^3, FP16-deviation storage"),
     "riemann": ("riemann", dict(), "fp64", "D2Q9 non-ideal Riemann problem 1000x4, FP64"),
     "shockdrop2d": ("shock_column", dict(D=2, shape=(4096, 2048), radius=128), "fp32",

@@ -98,7 +98,7 @@ enum { LBM_EOS_VDW = 0, LBM_EOS_PR = 1 };
  *   L = ln((1 + (1 + sqrt2) b rho) / (1 + (1 - sqrt2) b rho))
  * (the identity e = c_v T + int_0^rho (P - T dP/dT)/rho'^2 drho', c_v the
  * ideal-gas part); T(rho, e) is the positive root of a quadratic in sqrt(T),
- * taken in FP64 in every precision.  Peng-Robinson handles step with the exact
+ * taken in a form without cancellation in the arithmetic precision.  Peng-Robinson handles step with the exact
  * closure in FP32 or FP64 (fused or multipass); FP16-deviation storage, the
  * learned closure and batches are van der Waals only.
  * kappa: Korteweg capillarity coefficient, F = kappa rho grad lap rho (Eq. FK).

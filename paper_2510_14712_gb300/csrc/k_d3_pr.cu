@@ -1,5 +1,5 @@
 // Fused step with the exact Peng-Robinson closure: D = 3, FP32 and FP64 storage
-// and arithmetic (the temperature inversion in FP64 in both).
+// and arithmetic.
 #include "lbm_ops.cuh"
 
 namespace lbm {

@@ -109,12 +109,14 @@ template <typename real> __host__ __device__ inline real pr_cs2(const Model<real
   return dPdr + T * dPdT * dPdT / (rho * rho * pr_cv(m, rho, T));
 }
 // T from (rho, e): the positive root of c_v y^2 + A y + (B0 - e) = 0, y = sqrt(T), in
-// FP64 and in the form without cancellation, y = 2 (e - B0) / (A + sqrt(A^2 + 4 c_v (e - B0)))
-template <typename real> __host__ __device__ inline double pr_temperature(const Model<real>& m, real rho, real e) {
-  const double c = double(pr_c(m, rho)), a = m.a, k = m.mpr, cv = m.cv;
-  const double A = a * c * (1.0 + k) * k / sqrt(double(m.Tc)), B0 = -a * c * (1.0 + k) * (1.0 + k);
-  const double q = double(e) - B0;
-  const double y = 2.0 * q / (A + sqrt(A * A + 4.0 * cv * q));
+// the form without cancellation, y = 2 (e - B0) / (A + sqrt(A^2 + 4 c_v (e - B0))): every
+// term is positive, so the arithmetic precision of the kernel (FP32 or FP64) gives T to
+// a few of its ulps
+template <typename real> __host__ __device__ inline real pr_temperature(const Model<real>& m, real rho, real e) {
+  const real c = pr_c(m, rho), k = m.mpr;
+  const real A = m.a * c * (real(1) + k) * k / sqrt(m.Tc), B0 = -m.a * c * (real(1) + k) * (real(1) + k);
+  const real q = e - B0;
+  const real y = real(2) * q / (A + sqrt(A * A + real(4) * m.cv * q));
   return y * y;
 }
 
@@ -130,7 +132,7 @@ template <typename real> __host__ __device__ inline real eos_cs2(const Model<rea
 }
 // T from rho and the specific internal energy e (Eq. lbm_temp for van der Waals)
 template <typename real> __host__ __device__ inline real eos_temperature(const Model<real>& m, real rho, real e) {
-  return m.kind == LBM_EOS_PR ? real(pr_temperature(m, rho, e)) : (e + m.a * rho) / m.cv;
+  return m.kind == LBM_EOS_PR ? pr_temperature(m, rho, e) : (e + m.a * rho) / m.cv;
 }
 // the coefficients of grad s = c_T grad T - c_rho grad rho: c_v(rho, T)/T and (dP/dT)_rho / rho^2
 template <typename real>

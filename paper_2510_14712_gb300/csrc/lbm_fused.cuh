@@ -75,8 +75,8 @@ template <typename real> struct ExactClosure {
 };
 
 // Exact Peng-Robinson closure: T from the quadratic in sqrt(T) of its caloric
-// relation (FP64), then P and c_s^2 of the fluid; stage D reads P and c_s^2
-// from the centre ring (kExtra = 2) and e = h - P/rho.
+// relation, then P and c_s^2 of the fluid; stage D reads P and c_s^2 from the
+// centre ring (kExtra = 2) and e = h - P/rho.
 template <typename real> struct PrClosure {
   static constexpr bool kWarp = false;
   static constexpr int kExtra = 2;
@@ -84,7 +84,7 @@ template <typename real> struct PrClosure {
   __device__ __forceinline__ void load(const Params&, unsigned char*) {}
   __device__ __forceinline__ void operator()(const Model<real>& m, real rho, real e, bool, real& T, real& P,
                                              real& cs2) const {
-    T = real(pr_temperature(m, rho, e));
+    T = pr_temperature(m, rho, e);
     P = pr_pressure(m, rho, T);
     cs2 = pr_cs2(m, rho, T);
   }

@@ -4,8 +4,8 @@ oracle (oracle/eos.py, Newton's method for the temperature).
 
 Parity: relative L2 over the interior, 1e-12 (FP64) and 1e-5 (FP32; 5e-5 for the
 Riemann problem, the shock-carrying bound).  The kernels invert the caloric
-relation in closed form (a quadratic in sqrt(T), FP64), the oracle by Newton's
-method: both find the same unique root.
+relation in closed form (a quadratic in sqrt(T), in a form without cancellation),
+the oracle by Newton's method: both find the same unique root.
 """
 import numpy as np
 import pytest
