@@ -227,18 +227,20 @@ int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step);
 /* Shock capturing (Sec. 4.4, Eqs. shock_cap and shock_cap_k): numerical
  * transport coefficients added to the constant mu, eta, k of the handle,
  *   {mu, eta}^num = rho C_{mu,eta} F(|grad^4 S|),  k^num = rho c_s C_k F(|grad^4 |grad s||),
- * S the strain-rate magnitude |grad u + grad u^T|/2, grad s the van der
- * Waals entropy gradient (c_v/T) grad T - R/(rho (1 - b rho)) grad rho,
- * |grad^4 f| the norm of the per-axis five-point fourth differences
- * (r = 5, delta x = 1), F the separable binomial (1,4,6,4,1)/16 filter, c_s
- * the van der Waals sound speed at (rho, T).  The coefficients used by a
+ * S the strain-rate magnitude |grad u + grad u^T|/2, grad s the entropy
+ * gradient (c_v/T) grad T - R/(rho (1 - b rho)) grad rho of the van der
+ * Waals fluid (Peng-Robinson: (c_v(rho, T)/T) grad T - (dP/dT)_rho / rho^2
+ * grad rho, the same identity), |grad^4 f| the norm of the per-axis
+ * five-point fourth differences (r = 5, delta x = 1), F the separable
+ * binomial (1,4,6,4,1)/16 filter, c_s the fluid's sound speed at (rho, T).  The coefficients used by a
  * step are computed from the previous step's rho, u, T (none for the first
  * step after lbm_init).  All three C = 0 switches it off (the default).
  * The shear part is what stabilises planar shocks: with C_eta = 0 and
  * C_mu = C_k = 0.1 a D3Q27 Ma 1.2 shock 32 x 32 nodes wide stays stable,
  * Ma 1.25 needs 0.3 (without: blow-up within 100-200 steps).  C_eta > 0
  * enlarges the explicit bulk shift alpha (Eq. corr_bulk) and can
- * destabilise.  Costs D+2 planes written and D+3 extra launches per step.
+ * destabilise.  Costs D+2 planes written by the step and D+2 extra launches
+ * per step (the last filter pass fused with the coefficients).
  * Errors: LBM_EINVAL (NULL handle, negative or non-finite C), LBM_ENOMEM. */
 int lbm_set_shock_capturing(lbm_t h, double C_mu, double C_eta, double C_k);
 
