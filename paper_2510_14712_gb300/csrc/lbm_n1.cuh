@@ -48,6 +48,12 @@ __device__ __forceinline__ unsigned n1_nb(const Params& p, int x, int y, int z, 
 }
 
 // ---- per-node stages (shared by the single-instance and batched kernels) ----
+// No stage reads a buffer it writes, so every input goes through the read-only
+// path (__ldg), and each stage loads all its inputs before its first store: the
+// compiler cannot prove that the pointers (taken from the handle's parameters)
+// do not alias, and would otherwise order the later loads after the store.
+
+template <typename real> __device__ __forceinline__ real n1_ld(const real* q) { return __ldg(q); }
 
 // S and |grad s| at the node: out[0 .. plane) = S, out[plane ..) = |grad s|
 template <int D, typename real>
@@ -64,14 +70,15 @@ __device__ __forceinline__ void n1_strain_at(const Params& p, const real* __rest
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
-    for (int b = 0; b < D; ++b) g[a][b] = real(0.5) * (u[b * p.plane + op[a]] - u[b * p.plane + om[a]]);
+    for (int b = 0; b < D; ++b)
+      g[a][b] = real(0.5) * (n1_ld(u + b * p.plane + op[a]) - n1_ld(u + b * p.plane + om[a]));
   real acc = real(0);
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int b = 0; b < D; ++b) acc += (g[a][b] + g[b][a]) * (g[a][b] + g[b][a]);
-  out[o] = real(0.5) * sqrt(acc);
-  const real r = rho[o], t = T[o];
+  const real S = real(0.5) * sqrt(acc);
+  const real r = n1_ld(rho + o), t = n1_ld(T + o);
   real cT, cR;
   if (p.eos_kind == LBM_EOS_PR) {
     eos_entropy_coefs(model_of<real>(p), r, t, cT, cR);
@@ -82,10 +89,12 @@ __device__ __forceinline__ void n1_strain_at(const Params& p, const real* __rest
   real gs2 = real(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const real gT = real(0.5) * (T[op[a]] - T[om[a]]), gr = real(0.5) * (rho[op[a]] - rho[om[a]]);
+    const real gT = real(0.5) * (n1_ld(T + op[a]) - n1_ld(T + om[a]));
+    const real gr = real(0.5) * (n1_ld(rho + op[a]) - n1_ld(rho + om[a]));
     const real gs = cT * gT - cR * gr;
     gs2 += gs * gs;
   }
+  out[o] = S;
   out[p.plane + o] = sqrt(gs2);
 }
 
@@ -101,17 +110,21 @@ __device__ __forceinline__ void n1_d4_at(const Params& p, const real* __restrict
     nb[a][2] = n1_nb(p, x, y, z, o, a, 1);
     nb[a][3] = n1_nb(p, x, y, z, o, a, 2);
   }
+  real res[2];
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
     const real* v = in + f * p.plane;
     real acc = real(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const real d4 = v[nb[a][3]] - real(4) * v[nb[a][2]] + real(6) * v[o] - real(4) * v[nb[a][1]] + v[nb[a][0]];
+      const real d4 = n1_ld(v + nb[a][3]) - real(4) * n1_ld(v + nb[a][2]) + real(6) * n1_ld(v + o) -
+                      real(4) * n1_ld(v + nb[a][1]) + n1_ld(v + nb[a][0]);
       acc += d4 * d4;
     }
-    out[f * p.plane + o] = sqrt(acc);
+    res[f] = sqrt(acc);
   }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) out[f * p.plane + o] = res[f];
 }
 
 // binomial (1, 4, 6, 4, 1)/16 along axis a of field f of `in` at the node
@@ -121,14 +134,16 @@ __device__ __forceinline__ real n1_binomial(const Params& p, const real* __restr
   const unsigned m2 = n1_nb(p, x, y, z, o, a, -2), m1 = n1_nb(p, x, y, z, o, a, -1);
   const unsigned p1 = n1_nb(p, x, y, z, o, a, 1), p2 = n1_nb(p, x, y, z, o, a, 2);
   const real* v = in + f * p.plane;
-  return (v[m2] + real(4) * v[m1] + real(6) * v[o] + real(4) * v[p1] + v[p2]) / real(16);
+  return (n1_ld(v + m2) + real(4) * n1_ld(v + m1) + real(6) * n1_ld(v + o) + real(4) * n1_ld(v + p1) + n1_ld(v + p2)) /
+         real(16);
 }
 
 template <typename real>
 __device__ __forceinline__ void n1_filter_at(const Params& p, int a, const real* __restrict__ in,
                                              real* __restrict__ out, int x, int y, int z, unsigned o) {
-#pragma unroll
-  for (int f = 0; f < 2; ++f) out[f * p.plane + o] = n1_binomial(p, in, f, a, x, y, z, o);
+  const real s0 = n1_binomial(p, in, 0, a, x, y, z, o), s1 = n1_binomial(p, in, 1, a, x, y, z, o);
+  out[o] = s0;
+  out[p.plane + o] = s1;
 }
 
 // the last filter pass (along axis D-1) and the coefficients from the filtered
@@ -138,8 +153,8 @@ __device__ __forceinline__ void n1_filter_coef_at(const Params& p, const Model<r
                                                   const real* __restrict__ rho, const real* __restrict__ T,
                                                   real* __restrict__ visc, int x, int y, int z, unsigned o) {
   const real s4 = n1_binomial(p, in, 0, D - 1, x, y, z, o), g4 = n1_binomial(p, in, 1, D - 1, x, y, z, o);
-  const real r = rho[o];
-  const real cs2 = eos_cs2(m, r, T[o]);
+  const real r = n1_ld(rho + o);
+  const real cs2 = eos_cs2(m, r, n1_ld(T + o));
   const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
   visc[o] = r * real(p.sc_c[0]) * s4;
   visc[p.plane + o] = r * real(p.sc_c[1]) * s4;
@@ -184,7 +199,9 @@ template <int D, typename real> __global__ void k_n1_d4(Params p) {
 
 template <int D, typename real> __global__ void k_n1_filter(Params p, int a) {
   const N1Buffers<D, real> b(p);
-  n1_rows(p, [&](int x, int y, int z, unsigned o) { n1_filter_at<real>(p, a, b.filter_in(a), b.filter_out(a), x, y, z, o); });
+  n1_rows(p, [&](int x, int y, int z, unsigned o) {
+    n1_filter_at<real>(p, a, b.filter_in(a), b.filter_out(a), x, y, z, o);
+  });
 }
 
 template <int D, typename real>

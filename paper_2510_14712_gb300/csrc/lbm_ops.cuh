@@ -119,8 +119,18 @@ template <int D, typename S, typename real> struct OpsImpl {
         *fns = c;
         return 3;
       }
+    } else if constexpr (sizeof(real) == 4 && !CL::kWarp) {
+      // narrow tiles spread small domains (few columns) over more SMs; the
+      // 2-D FP32 body also fits 80 registers without spills, so 768 threads
+      // per SM (3 x 256, 6 x 128) can hide more of the latency of its short
+      // per-row stages
+      static const LaunchFn c[] = {&Fused<256, 1, 2, CL>::launch, &Fused<128, 1, 4, CL>::launch,
+                                   &Fused<512, 1, 1, CL>::launch, &Fused<64, 1, 8, CL>::launch,
+                                   &Fused<32, 1, 16, CL>::launch, &Fused<256, 1, 3, CL>::launch,
+                                   &Fused<128, 1, 6, CL>::launch};
+      *fns = c;
+      return 7;
     } else {
-      // narrow tiles spread small domains (few columns) over more SMs
       static const LaunchFn c[] = {&Fused<256, 1, 2, CL>::launch, &Fused<128, 1, 4, CL>::launch,
                                    &Fused<512, 1, 1, CL>::launch, &Fused<64, 1, 8, CL>::launch,
                                    &Fused<32, 1, 16, CL>::launch};
@@ -301,6 +311,15 @@ template <int D, typename S, typename real> struct OpsImpl {
         *pf = p; *ef = e;
         return 2;
       }
+    } else if constexpr (sizeof(real) == 4) {
+      static const PrepFn p[] = {&BatchFused<256, 1, 2>::prepare, &BatchFused<128, 1, 4>::prepare,
+                                 &BatchFused<64, 1, 8>::prepare, &BatchFused<256, 1, 3>::prepare,
+                                 &BatchFused<128, 1, 6>::prepare};
+      static const EnqFn e[] = {&BatchFused<256, 1, 2>::enqueue, &BatchFused<128, 1, 4>::enqueue,
+                                &BatchFused<64, 1, 8>::enqueue, &BatchFused<256, 1, 3>::enqueue,
+                                &BatchFused<128, 1, 6>::enqueue};
+      *pf = p; *ef = e;
+      return 5;
     } else {
       static const PrepFn p[] = {&BatchFused<256, 1, 2>::prepare, &BatchFused<128, 1, 4>::prepare,
                                  &BatchFused<64, 1, 8>::prepare};
