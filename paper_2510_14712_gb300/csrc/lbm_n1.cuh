@@ -21,17 +21,43 @@ namespace lbm {
 // v mod n for a shift of at most a few nodes: one comparison in range
 __device__ __forceinline__ int n1_wrap(int v, int n) { return unsigned(v) < unsigned(n) ? v : modp(v, n); }
 
+// Values a stage computes at one node, stored to K planes of its output.
+template <typename real, int K> struct N1Vals {
+  real v[K];
+};
+
+template <typename real, int K>
+__device__ __forceinline__ void n1_store(const Params& p, real* out, unsigned o, const N1Vals<real, K>& r) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k * p.plane + o] = r.v[k];
+}
+
 // Thread layout of the stencil kernels: threads along x, blocks along x and over
-// the rows (y, z), each block walking rows gridDim.y apart; f(x, y, z, o) for
-// every interior node of the thread, o its element offset in a plane (a plane
-// holds fewer than 2^31 elements: the buffers of a handle stay below 2^32
-// elements, checked at create).
-template <class F> __device__ __forceinline__ void n1_rows(const Params& p, F&& f) {
+// groups of kN1Rows consecutive rows (y, z), each block walking groups gridDim.y
+// apart.  f(x, y, z, o) computes the values of every interior node of the
+// thread, o its element offset in a plane (a plane holds fewer than 2^31
+// elements: the buffers of a handle stay below 2^32 elements, checked at
+// create).  The values of a whole group are computed before any is stored, so
+// that the loads of its rows can all be in flight together (the compiler
+// cannot move a load across a store to a pointer it cannot tell apart).
+constexpr int kN1Rows = 4;
+template <int K, typename real, class F>
+__device__ __forceinline__ void n1_rows(const Params& p, real* out, F&& f) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.Nx) return;
   const int rows = p.Ny * p.Nz;
-  for (int row = blockIdx.y; row < rows; row += gridDim.y)
-    f(x, row % p.Ny, row / p.Ny, unsigned(row) * unsigned(p.pitch) + unsigned(x + p.G));
+  auto off = [&](const int row) { return unsigned(row) * unsigned(p.pitch) + unsigned(x + p.G); };
+  for (int r0 = blockIdx.y * kN1Rows; r0 < rows; r0 += gridDim.y * kN1Rows) {
+    if (r0 + kN1Rows <= rows) {
+      N1Vals<real, K> res[kN1Rows];
+#pragma unroll
+      for (int r = 0; r < kN1Rows; ++r) res[r] = f(x, (r0 + r) % p.Ny, (r0 + r) / p.Ny, off(r0 + r));
+#pragma unroll
+      for (int r = 0; r < kN1Rows; ++r) n1_store(p, out, off(r0 + r), res[r]);
+    } else {
+      for (int row = r0; row < rows; ++row) n1_store(p, out, off(row), f(x, row % p.Ny, row / p.Ny, off(row)));
+    }
+  }
 }
 
 // offset of the interior neighbour (x, y, z) + s e_a of the node at offset o:
@@ -49,17 +75,15 @@ __device__ __forceinline__ unsigned n1_nb(const Params& p, int x, int y, int z, 
 
 // ---- per-node stages (shared by the single-instance and batched kernels) ----
 // No stage reads a buffer it writes, so every input goes through the read-only
-// path (__ldg), and each stage loads all its inputs before its first store: the
-// compiler cannot prove that the pointers (taken from the handle's parameters)
-// do not alias, and would otherwise order the later loads after the store.
+// path (__ldg).  Each returns its values; the caller stores them.
 
 template <typename real> __device__ __forceinline__ real n1_ld(const real* q) { return __ldg(q); }
 
-// S and |grad s| at the node: out[0 .. plane) = S, out[plane ..) = |grad s|
+// S and |grad s| at the node
 template <int D, typename real>
-__device__ __forceinline__ void n1_strain_at(const Params& p, const real* __restrict__ rho,
-                                             const real* __restrict__ u, const real* __restrict__ T,
-                                             real* __restrict__ out, int x, int y, int z, unsigned o) {
+__device__ __forceinline__ N1Vals<real, 2> n1_strain_at(const Params& p, const real* __restrict__ rho,
+                                                        const real* __restrict__ u, const real* __restrict__ T,
+                                                        int x, int y, int z, unsigned o) {
   unsigned op[D], om[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -94,14 +118,13 @@ __device__ __forceinline__ void n1_strain_at(const Params& p, const real* __rest
     const real gs = cT * gT - cR * gr;
     gs2 += gs * gs;
   }
-  out[o] = S;
-  out[p.plane + o] = sqrt(gs2);
+  return {{S, sqrt(gs2)}};
 }
 
 // norm of the per-axis fourth differences of the two fields of `in` at the node
 template <int D, typename real>
-__device__ __forceinline__ void n1_d4_at(const Params& p, const real* __restrict__ in, real* __restrict__ out,
-                                         int x, int y, int z, unsigned o) {
+__device__ __forceinline__ N1Vals<real, 2> n1_d4_at(const Params& p, const real* __restrict__ in, int x, int y, int z,
+                                                    unsigned o) {
   unsigned nb[D][4];                               // offsets of the -2, -1, +1, +2 neighbours along a
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -110,7 +133,7 @@ __device__ __forceinline__ void n1_d4_at(const Params& p, const real* __restrict
     nb[a][2] = n1_nb(p, x, y, z, o, a, 1);
     nb[a][3] = n1_nb(p, x, y, z, o, a, 2);
   }
-  real res[2];
+  N1Vals<real, 2> res;
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
     const real* v = in + f * p.plane;
@@ -121,10 +144,9 @@ __device__ __forceinline__ void n1_d4_at(const Params& p, const real* __restrict
                       real(4) * n1_ld(v + nb[a][1]) + n1_ld(v + nb[a][0]);
       acc += d4 * d4;
     }
-    res[f] = sqrt(acc);
+    res.v[f] = sqrt(acc);
   }
-#pragma unroll
-  for (int f = 0; f < 2; ++f) out[f * p.plane + o] = res[f];
+  return res;
 }
 
 // binomial (1, 4, 6, 4, 1)/16 along axis a of field f of `in` at the node
@@ -139,26 +161,23 @@ __device__ __forceinline__ real n1_binomial(const Params& p, const real* __restr
 }
 
 template <typename real>
-__device__ __forceinline__ void n1_filter_at(const Params& p, int a, const real* __restrict__ in,
-                                             real* __restrict__ out, int x, int y, int z, unsigned o) {
-  const real s0 = n1_binomial(p, in, 0, a, x, y, z, o), s1 = n1_binomial(p, in, 1, a, x, y, z, o);
-  out[o] = s0;
-  out[p.plane + o] = s1;
+__device__ __forceinline__ N1Vals<real, 2> n1_filter_at(const Params& p, int a, const real* __restrict__ in, int x,
+                                                        int y, int z, unsigned o) {
+  return {{n1_binomial(p, in, 0, a, x, y, z, o), n1_binomial(p, in, 1, a, x, y, z, o)}};
 }
 
 // the last filter pass (along axis D-1) and the coefficients from the filtered
-// norms: visc[0..2] planes = mu, eta, k numerical
+// norms: mu, eta, k numerical (the three planes of visc)
 template <int D, typename real>
-__device__ __forceinline__ void n1_filter_coef_at(const Params& p, const Model<real>& m, const real* __restrict__ in,
-                                                  const real* __restrict__ rho, const real* __restrict__ T,
-                                                  real* __restrict__ visc, int x, int y, int z, unsigned o) {
+__device__ __forceinline__ N1Vals<real, 3> n1_filter_coef_at(const Params& p, const Model<real>& m,
+                                                             const real* __restrict__ in, const real* __restrict__ rho,
+                                                             const real* __restrict__ T, int x, int y, int z,
+                                                             unsigned o) {
   const real s4 = n1_binomial(p, in, 0, D - 1, x, y, z, o), g4 = n1_binomial(p, in, 1, D - 1, x, y, z, o);
   const real r = n1_ld(rho + o);
   const real cs2 = eos_cs2(m, r, n1_ld(T + o));
   const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
-  visc[o] = r * real(p.sc_c[0]) * s4;
-  visc[p.plane + o] = r * real(p.sc_c[1]) * s4;
-  visc[2 * p.plane + o] = r * cs * real(p.sc_c[2]) * g4;
+  return {{r * real(p.sc_c[0]) * s4, r * real(p.sc_c[1]) * s4, r * cs * real(p.sc_c[2]) * g4}};
 }
 
 // Buffers of one handle's shock capturing: the step's rho, u (D planes), T (by
@@ -189,27 +208,27 @@ template <int D, typename real>
 __global__ void k_n1_strain(Params p, const real* __restrict__ rho, const real* __restrict__ u,
                             const real* __restrict__ T) {
   const N1Buffers<D, real> b(p, rho, u, T);
-  n1_rows(p, [&](int x, int y, int z, unsigned o) { n1_strain_at<D, real>(p, b.rho, b.u, b.T, b.w0, x, y, z, o); });
+  n1_rows<2>(p, b.w0,
+             [&](int x, int y, int z, unsigned o) { return n1_strain_at<D, real>(p, b.rho, b.u, b.T, x, y, z, o); });
 }
 
 template <int D, typename real> __global__ void k_n1_d4(Params p) {
   const N1Buffers<D, real> b(p);
-  n1_rows(p, [&](int x, int y, int z, unsigned o) { n1_d4_at<D, real>(p, b.w0, b.w1, x, y, z, o); });
+  n1_rows<2>(p, b.w1, [&](int x, int y, int z, unsigned o) { return n1_d4_at<D, real>(p, b.w0, x, y, z, o); });
 }
 
 template <int D, typename real> __global__ void k_n1_filter(Params p, int a) {
   const N1Buffers<D, real> b(p);
-  n1_rows(p, [&](int x, int y, int z, unsigned o) {
-    n1_filter_at<real>(p, a, b.filter_in(a), b.filter_out(a), x, y, z, o);
-  });
+  n1_rows<2>(p, b.filter_out(a),
+             [&](int x, int y, int z, unsigned o) { return n1_filter_at<real>(p, a, b.filter_in(a), x, y, z, o); });
 }
 
 template <int D, typename real>
 __global__ void k_n1_filter_coef(Params p, const real* __restrict__ rho, const real* __restrict__ T) {
   const N1Buffers<D, real> b(p, rho, nullptr, T);
   const Model<real> m = model_of<real>(p);
-  n1_rows(p, [&](int x, int y, int z, unsigned o) {
-    n1_filter_coef_at<D, real>(p, m, b.filter_in(D - 1), b.rho, b.T, b.visc, x, y, z, o);
+  n1_rows<3>(p, b.visc, [&](int x, int y, int z, unsigned o) {
+    return n1_filter_coef_at<D, real>(p, m, b.filter_in(D - 1), b.rho, b.T, x, y, z, o);
   });
 }
 
@@ -217,7 +236,8 @@ __global__ void k_n1_filter_coef(Params p, const real* __restrict__ rho, const r
 // T (padded plane layout): D + 2 launches.
 template <int D, typename real>
 inline int n1_update(const Params& p, cudaStream_t st, const real* rho, const real* u, const real* T) {
-  const dim3 block(128), grid(unsigned((p.Nx + 127) / 128), unsigned(p.Ny * p.Nz < 65535 ? p.Ny * p.Nz : 65535));
+  const int groups = (p.Ny * p.Nz + kN1Rows - 1) / kN1Rows;
+  const dim3 block(128), grid(unsigned((p.Nx + 127) / 128), unsigned(groups < 65535 ? groups : 65535));
   k_n1_strain<D, real><<<grid, block, 0, st>>>(p, rho, u, T);
   k_n1_d4<D, real><<<grid, block, 0, st>>>(p);
   for (int a = 0; a + 1 < D; ++a) k_n1_filter<D, real><<<grid, block, 0, st>>>(p, a);
@@ -250,10 +270,11 @@ __global__ void k_n1_batch(const BatchInstance* __restrict__ insts, const int* _
   const Model<real> m = model_of<real>(p);
   for (int x = threadIdx.x; x < p.Nx; x += blockDim.x) {
     const unsigned o = unsigned(row) * unsigned(p.pitch) + unsigned(x + p.G);
-    if constexpr (STAGE == 0) n1_strain_at<D, real>(p, b.rho, b.u, b.T, b.w0, x, y, z, o);
-    else if constexpr (STAGE == 1) n1_d4_at<D, real>(p, b.w0, b.w1, x, y, z, o);
-    else if constexpr (STAGE == 2) n1_filter_at<real>(p, a, b.filter_in(a), b.filter_out(a), x, y, z, o);
-    else n1_filter_coef_at<D, real>(p, m, b.filter_in(D - 1), b.rho, b.T, b.visc, x, y, z, o);
+    if constexpr (STAGE == 0) n1_store(p, b.w0, o, n1_strain_at<D, real>(p, b.rho, b.u, b.T, x, y, z, o));
+    else if constexpr (STAGE == 1) n1_store(p, b.w1, o, n1_d4_at<D, real>(p, b.w0, x, y, z, o));
+    else if constexpr (STAGE == 2)
+      n1_store(p, b.filter_out(a), o, n1_filter_at<real>(p, a, b.filter_in(a), x, y, z, o));
+    else n1_store(p, b.visc, o, n1_filter_coef_at<D, real>(p, m, b.filter_in(D - 1), b.rho, b.T, x, y, z, o));
   }
 }
 
