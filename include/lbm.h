@@ -261,6 +261,19 @@ int lbm_set_graphs(lbm_t h, int on);
  * a NULL handle. */
 int lbm_autotune_times(lbm_t h, float* ms_per_step, int n);
 
+/* Number of tile shapes of the fused step kernel for this handle's lattice,
+ * precision and closure (the candidates lbm_autotune times, in its order).
+ * Returns the count (>= 1), or LBM_EINVAL for a NULL handle. */
+int lbm_tile_count(lbm_t h);
+
+/* Use tile shape `index` (0 <= index < lbm_tile_count(h); 0 is the default)
+ * for the fused step from now on, instead of the autotuner's choice.  Every
+ * shape computes the same step.  The setting lasts until the next lbm_init,
+ * lbm_autotune or closure change (those re-select the remembered or default
+ * shape).  Does not synchronise.
+ * Errors: LBM_EINVAL (NULL handle, index out of range). */
+int lbm_set_tile(lbm_t h, int index);
+
 /* Kernel launches enqueued by this handle since creation (for accounting). */
 long long lbm_launch_count(lbm_t h);
 

@@ -32,7 +32,8 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
 EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_init_device",
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
-           "lbm_set_step_kernel", "lbm_autotune", "lbm_autotune_times", "lbm_set_graphs",
+           "lbm_set_step_kernel", "lbm_autotune", "lbm_autotune_times", "lbm_tile_count", "lbm_set_tile",
+           "lbm_set_graphs",
            "lbm_set_shock_capturing", "lbm_launch_count",
            "lbm_destroy",
            "lbm_last_error", "lbm_version",
@@ -95,6 +96,8 @@ def load():
         "lbm_set_step_kernel": (I, [P, I]),
         "lbm_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]),
         "lbm_autotune_times": (I, [P, P, I]),
+        "lbm_tile_count": (I, [P]),
+        "lbm_set_tile": (I, [P, I]),
         "lbm_set_graphs": (I, [P, I]),
         "lbm_set_shock_capturing": (I, [P, D, D, D]),
         "lbm_launch_count": (ctypes.c_longlong, [P]),
@@ -284,6 +287,19 @@ def lbm_set_shock_capturing(h, C_mu=0.1, C_eta=0.0, C_k=0.1):
 
 def lbm_set_graphs(h, on=True):
     _check(load().lbm_set_graphs(h, 1 if on else 0))
+
+
+def lbm_tile_count(h):
+    """Number of tile shapes of the fused step for this handle."""
+    n = load().lbm_tile_count(h)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def lbm_set_tile(h, index):
+    """Use tile shape `index` of the fused step until the next init / autotune."""
+    _check(load().lbm_set_tile(h, int(index)))
 
 
 def lbm_autotune_times(h):

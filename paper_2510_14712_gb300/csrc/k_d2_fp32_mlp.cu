@@ -8,4 +8,5 @@ void step_d2_fp32_mlp(Handle& h, const void* src, void* dst) {
 int autotune_d2_fp32_mlp(Handle& h, int reps, float* best_ms) {
   return OpsImpl<2, float, float>::autotune_cl<MlpClosure>(h, reps, best_ms);
 }
+int ntiles_d2_fp32_mlp() { return OpsImpl<2, float, float>::ntiles_cl<MlpClosure>(); }
 }  // namespace lbm

@@ -9,10 +9,12 @@ void step_d3_fp32_pr(Handle& h, const void* src, void* dst) {
 int autotune_d3_fp32_pr(Handle& h, int reps, float* best_ms) {
   return OpsImpl<3, float, float>::autotune_cl<PrClosure<float>>(h, reps, best_ms);
 }
+int ntiles_d3_fp32_pr() { return OpsImpl<3, float, float>::ntiles_cl<PrClosure<float>>(); }
 void step_d3_fp64_pr(Handle& h, const void* src, void* dst) {
   OpsImpl<3, double, double>::step_cl<PrClosure<double>>(h, src, dst);
 }
 int autotune_d3_fp64_pr(Handle& h, int reps, float* best_ms) {
   return OpsImpl<3, double, double>::autotune_cl<PrClosure<double>>(h, reps, best_ms);
 }
+int ntiles_d3_fp64_pr() { return OpsImpl<3, double, double>::ntiles_cl<PrClosure<double>>(); }
 }  // namespace lbm

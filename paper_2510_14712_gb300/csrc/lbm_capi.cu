@@ -43,10 +43,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 // Exact-closure table with the fused step and the autotuner swapped for the
 // learned-closure ones (multi-pass and batched steps are exact-only).
-Ops with_mlp(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*)) {
+Ops with_mlp(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*),
+              int (*ntiles)()) {
   Ops o = *base;
   o.step = step;
   o.autotune = tune;
+  o.ntiles = ntiles;
   o.step_multipass = nullptr;
   o.batch_ncfg = nullptr;
   o.batch_prepare = nullptr;
@@ -56,10 +58,12 @@ Ops with_mlp(const Ops* base, void (*step)(Handle&, const void*, void*), int (*t
 
 // Exact-closure table with the fused step and the autotuner of the Peng-Robinson
 // closure (the multi-pass step is EOS-generic; batches are van der Waals only).
-Ops with_pr(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*)) {
+Ops with_pr(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*),
+             int (*ntiles)()) {
   Ops o = *base;
   o.step = step;
   o.autotune = tune;
+  o.ntiles = ntiles;
   o.batch_ncfg = nullptr;
   o.batch_prepare = nullptr;
   o.batch_enqueue = nullptr;
@@ -68,16 +72,16 @@ Ops with_pr(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tu
 
 const Ops* ops_for(const Handle& h) {
   if (h.p.eos_kind == LBM_EOS_PR) {
-    static const Ops p2f = with_pr(ops_d2_fp32(), step_d2_fp32_pr, autotune_d2_fp32_pr);
-    static const Ops p3f = with_pr(ops_d3_fp32(), step_d3_fp32_pr, autotune_d3_fp32_pr);
-    static const Ops p2d = with_pr(ops_d2_fp64(), step_d2_fp64_pr, autotune_d2_fp64_pr);
-    static const Ops p3d = with_pr(ops_d3_fp64(), step_d3_fp64_pr, autotune_d3_fp64_pr);
+    static const Ops p2f = with_pr(ops_d2_fp32(), step_d2_fp32_pr, autotune_d2_fp32_pr, ntiles_d2_fp32_pr);
+    static const Ops p3f = with_pr(ops_d3_fp32(), step_d3_fp32_pr, autotune_d3_fp32_pr, ntiles_d3_fp32_pr);
+    static const Ops p2d = with_pr(ops_d2_fp64(), step_d2_fp64_pr, autotune_d2_fp64_pr, ntiles_d2_fp64_pr);
+    static const Ops p3d = with_pr(ops_d3_fp64(), step_d3_fp64_pr, autotune_d3_fp64_pr, ntiles_d3_fp64_pr);
     if (h.precision == LBM_FP64) return h.D == 2 ? &p2d : &p3d;
     return h.D == 2 ? &p2f : &p3f;
   }
   if (h.closure == LBM_CLOSURE_MLP) {
-    static const Ops m2 = with_mlp(ops_d2_fp32(), step_d2_fp32_mlp, autotune_d2_fp32_mlp);
-    static const Ops m3 = with_mlp(ops_d3_fp32(), step_d3_fp32_mlp, autotune_d3_fp32_mlp);
+    static const Ops m2 = with_mlp(ops_d2_fp32(), step_d2_fp32_mlp, autotune_d2_fp32_mlp, ntiles_d2_fp32_mlp);
+    static const Ops m3 = with_mlp(ops_d3_fp32(), step_d3_fp32_mlp, autotune_d3_fp32_mlp, ntiles_d3_fp32_mlp);
     return h.D == 2 ? &m2 : &m3;
   }
   if (h.D == 2) {
@@ -603,6 +607,20 @@ int lbm_autotune_times(lbm_t h, float* ms_per_step, int n) {
   for (int k = 0; k < h->tune_n && k < n; ++k)
     if (ms_per_step) ms_per_step[k] = h->tune_ms[k];
   return h->tune_n;
+}
+
+int lbm_tile_count(lbm_t h) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  return ops_for(*h)->ntiles();
+}
+
+int lbm_set_tile(lbm_t h, int index) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  const int n = ops_for(*h)->ntiles();
+  if (index < 0 || index >= n)
+    return fail(LBM_EINVAL, "tile index " + std::to_string(index) + " out of range [0, " + std::to_string(n) + ")");
+  h->tile_cfg = index;                 // step graphs are re-captured (they record the tile)
+  return LBM_OK;
 }
 
 long long lbm_launch_count(lbm_t h) { return h ? h->launches : 0; }

@@ -105,6 +105,8 @@ struct Ops {
   int (*batch_ncfg)();
   int (*batch_prepare)(Batch& b, int cfg);
   void (*batch_enqueue)(Batch& b, int parity);
+  // number of tile shapes of the fused step (indices of lbm_set_tile / lbm_autotune)
+  int (*ntiles)();
 };
 
 // A batch of instances stepped together (lbm_batch_* in include/lbm.h).
@@ -159,5 +161,11 @@ int autotune_d2_fp64_pr(Handle& h, int reps, float* best_ms);
 int autotune_d3_fp64_pr(Handle& h, int reps, float* best_ms);
 int autotune_d2_fp32_mlp(Handle& h, int reps, float* best_ms);
 int autotune_d3_fp32_mlp(Handle& h, int reps, float* best_ms);
+int ntiles_d2_fp32_pr();
+int ntiles_d3_fp32_pr();
+int ntiles_d2_fp64_pr();
+int ntiles_d3_fp64_pr();
+int ntiles_d2_fp32_mlp();
+int ntiles_d3_fp32_mlp();
 
 }  // namespace lbm

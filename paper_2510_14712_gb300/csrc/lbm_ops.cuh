@@ -199,6 +199,11 @@ template <int D, typename S, typename real> struct OpsImpl {
     return best;
   }
   static int autotune(Handle& h, int reps, float* best_ms) { return autotune_cl<ExactClosure<real>>(h, reps, best_ms); }
+  template <class CL> static int ntiles_cl() {
+    const LaunchFn* fns;
+    return candidates<CL>(&fns);
+  }
+  static int ntiles() { return ntiles_cl<ExactClosure<real>>(); }
 
   static void step_multipass(Handle& h, const void* src, void* dst) {
     const Params& p = h.p;
@@ -348,7 +353,8 @@ template <int D, typename S, typename real> struct OpsImpl {
   }
 
   static const Ops* ops() {
-    static const Ops o = {&init, &step, &step_multipass, &macro, &autotune, &batch_ncfg, &batch_prepare, &batch_enqueue};
+    static const Ops o = {&init,       &step,          &step_multipass, &macro, &autotune,
+                          &batch_ncfg, &batch_prepare, &batch_enqueue,  &ntiles};
     return &o;
   }
 };

@@ -282,6 +282,45 @@ def test_autotune_keeps_state_and_results(D):
         assert rel_l2(a[k], b[k]) < 1e-6
 
 
+TILE_CASES = [
+    ("d2 riemann 700x5 fp32", lambda: inputs.add_noise(inputs.riemann(Nx=700, Ny=5), 1), "fp32"),
+    ("d2 riemann 700x5 fp16dev", lambda: inputs.add_noise(inputs.riemann(Nx=700, Ny=5), 1), "fp16dev"),
+    ("d2 riemann 300x7 fp64", lambda: inputs.add_noise(inputs.riemann(Nx=300, Ny=7), 2), "fp64"),
+    ("d2 couette walls 600x3 fp32", lambda: inputs.couette(2, (600, 3), Ma=0.5, seed=3, rel=1e-2), "fp32"),
+    ("d3 tgv 40x27x18 fp32", lambda: tgv_case((40, 27, 18)), "fp32"),
+]
+
+
+@pytest.mark.parametrize("name,make,precision", TILE_CASES, ids=[t[0] for t in TILE_CASES])
+def test_every_tile_shape_gives_the_same_step(name, make, precision):
+    """lbm_set_tile: every tile shape of the fused step (ragged last column
+    tiles, wall faces, plain launches and graph replay) gives the step of shape 0."""
+    c = make()
+    s = P.Solver(c, precision=precision)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    try:
+        s.init()
+        n = P.lbm_tile_count(s.h)
+        assert n >= 1
+        for bad in (-1, n):
+            with pytest.raises(P.LbmError):
+                P.lbm_set_tile(s.h, bad)
+        ref = None
+        for k in range(n):
+            s.init()
+            P.lbm_set_tile(s.h, k)
+            P.lbm_set_graphs(s.h, k % 2 == 1)
+            s.step(12)
+            got = s.fields()
+            if ref is None:
+                ref = got
+                continue
+            for key in ("rho", "u", "T"):
+                assert rel_l2(got[key], ref[key]) < tol, "%s tile %d of %d: %s" % (name, k, n, key)
+    finally:
+        s.close()
+
+
 def test_riemann_chunked_equals_single_call():
     a = gpu_run(inputs.riemann(Nx=200, Ny=4), 60, "fp32")
     b = gpu_run(inputs.riemann(Nx=200, Ny=4), 60, "fp32", chunk=7)
