@@ -64,6 +64,40 @@ def test_fourth_difference_and_binomial_filter():
     assert np.allclose(lbm.binomial_filter(delta, 2, [True, True])[8:13, 10:15], np.outer(w, w), rtol=1e-14)
 
 
+def coefficient_errors(transport):
+    """Largest relative errors of (mu, eta, k)^num from `transport` against closed forms.
+
+    The two fields have filtered fourth-difference norms that are known exactly.
+    - u_x = c y^5/120, u_y = 0. The central-difference strain magnitude is
+      S = c (y^4/24 + y^2/12 + 1/120) / sqrt2, a quartic in y. Its five-point fourth
+      difference is c/sqrt2, a constant that the normalised filter keeps.
+    - b = 0, uniform T, rho = exp(lam x^2 / 2). Then |grad s| = R e^(lam/2) sinh(lam x).
+      The fourth difference multiplies sinh(lam x) by 16 sinh^4(lam/2), and the
+      (1, 4, 6, 4, 1)/16 filter multiplies it by cosh^4(lam/2). Together that is
+      R e^(lam/2) sinh^4(lam) sinh(lam x).
+    c_s^2 is a given non-uniform field. Compared on the nodes at least six away from
+    the clamped faces.
+    """
+    nx, ny = 24, 20
+    x, y = grid2(nx, ny)
+    c, lam, R, cv = 1e-3, 0.2, 8.0 / 3.0, 8.0
+    rho = np.exp(lam * x * x / 2.0)
+    u = [c * y ** 5 / 120.0, 0.0 * x]
+    T = 0.1 + 0.0 * x
+    cs2 = 0.2 + 0.05 * np.cos(0.3 * x + 0.2 * y)
+    coef = (0.3, 0.7, 0.11)
+    got = transport(rho, u, T, cs2, coef, 0.0, R, cv, 2, [False, False])
+    s4 = c / math.sqrt(2.0)
+    g4 = R * math.exp(lam / 2.0) * math.sinh(lam) ** 4 * np.sinh(lam * x)
+    want = (rho * coef[0] * s4, rho * coef[1] * s4, rho * np.sqrt(cs2) * coef[2] * g4)
+    inner = (slice(6, -6), slice(6, -6))
+    return [float(np.abs(g[inner] / w[inner] - 1.0).max()) for g, w in zip(got, want)]
+
+
+def test_coefficients_of_fields_with_known_filtered_norms():
+    assert max(coefficient_errors(lbm.numerical_transport)) < 1e-9
+
+
 def test_uniform_state_and_zero_coefficients_give_zero():
     sh = (6, 8)
     rho, T = 0.4 + np.zeros(sh), 0.1 + np.zeros(sh)

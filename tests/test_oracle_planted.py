@@ -164,3 +164,61 @@ def test_departure_energy_without_alpha_slope_breaks_caloric_pin(monkeypatch):
                         lambda self, rho, T: -self.a * self.alpha(T) * self._L(rho) / (2.0 * oeos.SQRT2 * self.b))
     with pytest.raises(AssertionError):
         tp.test_caloric_relation_against_quadrature(0.6, 1.05)
+
+
+# ---- shock capturing (Sec. 4.4): the coefficient assembly and its building blocks ----
+
+def _n1_pin_fails():
+    import test_oracle_n1 as n1
+    return max(n1.coefficient_errors(lbm.numerical_transport)) > 1e-6
+
+
+def test_swapped_shear_and_conduction_constants_break_coefficient_pin(monkeypatch):
+    orig = lbm.numerical_transport
+
+    def swapped(rho, u, T, cs2, coef, *rest, **kw):
+        return orig(rho, u, T, cs2, (coef[2], coef[1], coef[0]), *rest, **kw)
+    monkeypatch.setattr(lbm, "numerical_transport", swapped)
+    assert _n1_pin_fails()
+
+
+def test_conductivity_without_sound_speed_breaks_coefficient_pin(monkeypatch):
+    orig = lbm.numerical_transport
+
+    def no_cs(rho, u, T, cs2, coef, *rest, **kw):
+        return orig(rho, u, T, np.ones_like(cs2), coef, *rest, **kw)
+    monkeypatch.setattr(lbm, "numerical_transport", no_cs)
+    assert _n1_pin_fails()
+
+
+def test_three_point_filter_breaks_coefficient_pin(monkeypatch):
+    def filter121(f, D, per):
+        for a in range(D):
+            f = (lbm._shift(f, a, -1, D, per[a]) + 2.0 * f + lbm._shift(f, a, 1, D, per[a])) / 4.0
+        return f
+    monkeypatch.setattr(lbm, "binomial_filter", filter121)
+    assert _n1_pin_fails()
+
+
+def test_unsymmetrised_velocity_gradient_breaks_coefficient_pin(monkeypatch):
+    def grad_norm(u, D, per):
+        g = [[0.5 * (lbm._shift(u[b], a, 1, D, per[a]) - lbm._shift(u[b], a, -1, D, per[a])) for b in range(D)]
+             for a in range(D)]
+        return np.sqrt(sum(g[a][b] ** 2 for a in range(D) for b in range(D)))
+    monkeypatch.setattr(lbm, "strain_rate_magnitude", grad_norm)
+    assert _n1_pin_fails()
+
+
+def test_flipped_density_term_of_entropy_gradient_breaks_isentrope_pin(monkeypatch):
+    import test_oracle_n1 as n1
+
+    def flipped(rho, T, b, R, cv, D, per, fluid=None):
+        gs = []
+        for a in range(D):
+            gT = 0.5 * (lbm._shift(T, a, 1, D, per[a]) - lbm._shift(T, a, -1, D, per[a]))
+            gr = 0.5 * (lbm._shift(rho, a, 1, D, per[a]) - lbm._shift(rho, a, -1, D, per[a]))
+            gs.append(cv / T * gT + R / (rho * (1.0 - b * rho)) * gr)
+        return np.sqrt(sum(x * x for x in gs))
+    monkeypatch.setattr(lbm, "entropy_gradient_magnitude", flipped)
+    with pytest.raises(AssertionError):
+        n1.test_entropy_gradient_of_isothermal_ramp_and_isentrope()
