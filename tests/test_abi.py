@@ -64,6 +64,8 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.lbm_step(None, 1) == P.LBM_EINVAL
     assert lib.lbm_moments(None, None, None, None, None) == P.LBM_EINVAL
     assert lib.lbm_population_bytes(None) == 0
+    assert lib.lbm_tile_count(None) == P.LBM_EINVAL
+    assert lib.lbm_set_tile(None, 0) == P.LBM_EINVAL
     assert lib.lbm_version().startswith(b"gb300")
 
 
