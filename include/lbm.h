@@ -6,8 +6,9 @@
  * One step of the method, at every node (Sec. 3.2 and Fig. FlowChart):
  * pull-stream the mass-momentum populations f_i and the bulk-energy
  * populations g_i, take the moments rho, rho u, rho E (Eqs. def_h, def_u,
- * def_E), evaluate the van der Waals EOS and the explicit temperature
- * (Eqs. Pvdw, lbm_temp), build the Korteweg force, the Galilean correction
+ * def_E), evaluate the equation of state and the temperature (van der
+ * Waals: Eqs. Pvdw, lbm_temp, explicit; Peng-Robinson: a closed-form root of
+ * its caloric relation), build the Korteweg force, the Galilean correction
  * Phi and the heat-flux correction q^c from neighbour moments (Eqs. FK,
  * correction, qc_1), form the equilibria and shifted equilibria in product
  * form (Eqs. LBMeq, LBMstar, LBMeqG, LBMgstar) and collide (Eqs. fLBGK,
@@ -30,10 +31,14 @@
  *    inspection, and refuses further steps with LBM_ESTATE until lbm_init.
  *
  * Boundaries: y and z are periodic.  The two x faces are either both
- * periodic, or each is an inflow face (post-collision populations of four
- * ghost layers set to the equilibrium of a prescribed state, every step) or
- * a zero-gradient outflow face (ghost layers copy the nearest interior
- * layer).  The paper gives no boundary scheme; this is the library's.
+ * periodic, or each is one of:
+ *  - an inflow face: post-collision populations of four ghost layers set to
+ *    the equilibrium of a prescribed state, every step;
+ *  - a zero-gradient outflow face: the ghost layers copy the nearest
+ *    interior layer;
+ *  - a moving isothermal wall: diffuse reflection at the wall velocity and
+ *    temperature (LBM_BC_WALL, lbm_set_boundary).
+ * The paper gives no boundary scheme; these are the library's.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -98,9 +103,10 @@ enum { LBM_EOS_VDW = 0, LBM_EOS_PR = 1 };
  *   L = ln((1 + (1 + sqrt2) b rho) / (1 + (1 - sqrt2) b rho))
  * (the identity e = c_v T + int_0^rho (P - T dP/dT)/rho'^2 drho', c_v the
  * ideal-gas part); T(rho, e) is the positive root of a quadratic in sqrt(T),
- * taken in a form without cancellation in the arithmetic precision.  Peng-Robinson handles step with the exact
- * closure in FP32 or FP64 (fused or multipass); FP16-deviation storage, the
- * learned closure and batches are van der Waals only.
+ * taken in a form without cancellation in the arithmetic precision.
+ * Peng-Robinson handles step with the exact closure in FP32 or FP64 (fused
+ * or multipass); FP16-deviation storage, the learned closure and batches are
+ * van der Waals only.
  * kappa: Korteweg capillarity coefficient, F = kappa rho grad lap rho (Eq. FK).
  * eta_over_mu: bulk to shear viscosity ratio entering alpha (Eq. corr_bulk).
  * rho_ref, T_ref: reference state fixing the constant mu = tau P(rho_ref, T_ref)
@@ -127,7 +133,8 @@ typedef struct {
  * Allocates the device state (two population buffers, scratch).  Both x faces
  * start periodic.  Errors: LBM_EINVAL (out is NULL, lattice not 9/27, a size
  * < 1, Nz != 1 with D2Q9, a non-positive tau, Pr, cv, b rho_ref >= 1,
- * unsupported precision/closure), LBM_ENOMEM, LBM_ECUDA. */
+ * unsupported kind/precision/closure, a Peng-Robinson fluid with Tc <= 0,
+ * m < 0 or FP16-deviation storage), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* eos,
                double tau, double Pr, double cv);
 
