@@ -246,8 +246,10 @@ int lbm_autotune(lbm_t h, int reps, int* chosen, float* ms_per_step);
  * C_mu = C_k = 0.1 a D3Q27 Ma 1.2 shock 32 x 32 nodes wide stays stable,
  * Ma 1.25 needs 0.3 (without: blow-up within 100-200 steps).  C_eta > 0
  * enlarges the explicit bulk shift alpha (Eq. corr_bulk) and can
- * destabilise.  Costs D+2 planes written by the step and D+2 extra launches
- * per step (the last filter pass fused with the coefficients).
+ * destabilise.  Costs D+2 planes written by the step and extra launches per
+ * step: 2 in 2-D (strain with fourth differences over shared-memory tiles;
+ * both filter passes with the coefficients), D+2 in 3-D (the last filter pass
+ * fused with the coefficients).
  * Errors: LBM_EINVAL (NULL handle, negative or non-finite C), LBM_ENOMEM. */
 int lbm_set_shock_capturing(lbm_t h, double C_mu, double C_eta, double C_k);
 

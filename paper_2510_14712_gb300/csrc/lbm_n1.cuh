@@ -79,6 +79,25 @@ __device__ __forceinline__ unsigned n1_nb(const Params& p, int x, int y, int z, 
 
 template <typename real> __device__ __forceinline__ real n1_ld(const real* q) { return __ldg(q); }
 
+// five-point fourth difference and binomial (1, 4, 6, 4, 1)/16 of the values at
+// offsets -2 .. +2 along one axis, and the coefficients from the filtered norms
+// (one definition for the row-mapped and the tiled forms)
+template <typename real>
+__device__ __forceinline__ real n1_fourth(real vm2, real vm1, real v0, real vp1, real vp2) {
+  return vp2 - real(4) * vp1 + real(6) * v0 - real(4) * vm1 + vm2;
+}
+template <typename real>
+__device__ __forceinline__ real n1_binom5(real vm2, real vm1, real v0, real vp1, real vp2) {
+  return (vm2 + real(4) * vm1 + real(6) * v0 + real(4) * vp1 + vp2) / real(16);
+}
+template <typename real>
+__device__ __forceinline__ N1Vals<real, 3> n1_coefs(const Params& p, const Model<real>& m, real r, real t, real s4,
+                                                    real g4) {
+  const real cs2 = eos_cs2(m, r, t);
+  const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
+  return {{r * real(p.sc_c[0]) * s4, r * real(p.sc_c[1]) * s4, r * cs * real(p.sc_c[2]) * g4}};
+}
+
 // S and |grad s| at the node
 template <int D, typename real>
 __device__ __forceinline__ N1Vals<real, 2> n1_strain_at(const Params& p, const real* __restrict__ rho,
@@ -140,8 +159,8 @@ __device__ __forceinline__ N1Vals<real, 2> n1_d4_at(const Params& p, const real*
     real acc = real(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const real d4 = n1_ld(v + nb[a][3]) - real(4) * n1_ld(v + nb[a][2]) + real(6) * n1_ld(v + o) -
-                      real(4) * n1_ld(v + nb[a][1]) + n1_ld(v + nb[a][0]);
+      const real d4 = n1_fourth(n1_ld(v + nb[a][0]), n1_ld(v + nb[a][1]), n1_ld(v + o), n1_ld(v + nb[a][2]),
+                                n1_ld(v + nb[a][3]));
       acc += d4 * d4;
     }
     res.v[f] = sqrt(acc);
@@ -156,8 +175,7 @@ __device__ __forceinline__ real n1_binomial(const Params& p, const real* __restr
   const unsigned m2 = n1_nb(p, x, y, z, o, a, -2), m1 = n1_nb(p, x, y, z, o, a, -1);
   const unsigned p1 = n1_nb(p, x, y, z, o, a, 1), p2 = n1_nb(p, x, y, z, o, a, 2);
   const real* v = in + f * p.plane;
-  return (n1_ld(v + m2) + real(4) * n1_ld(v + m1) + real(6) * n1_ld(v + o) + real(4) * n1_ld(v + p1) + n1_ld(v + p2)) /
-         real(16);
+  return n1_binom5(n1_ld(v + m2), n1_ld(v + m1), n1_ld(v + o), n1_ld(v + p1), n1_ld(v + p2));
 }
 
 template <typename real>
@@ -174,10 +192,7 @@ __device__ __forceinline__ N1Vals<real, 3> n1_filter_coef_at(const Params& p, co
                                                              const real* __restrict__ T, int x, int y, int z,
                                                              unsigned o) {
   const real s4 = n1_binomial(p, in, 0, D - 1, x, y, z, o), g4 = n1_binomial(p, in, 1, D - 1, x, y, z, o);
-  const real r = n1_ld(rho + o);
-  const real cs2 = eos_cs2(m, r, n1_ld(T + o));
-  const real cs = sqrt(cs2 > real(0) ? cs2 : real(0));
-  return {{r * real(p.sc_c[0]) * s4, r * real(p.sc_c[1]) * s4, r * cs * real(p.sc_c[2]) * g4}};
+  return n1_coefs(p, m, n1_ld(rho + o), n1_ld(T + o), s4, g4);
 }
 
 // Buffers of one handle's shock capturing: the step's rho, u (D planes), T (by
@@ -232,17 +247,116 @@ __global__ void k_n1_filter_coef(Params p, const real* __restrict__ rho, const r
   });
 }
 
+// ---- 2-D single-instance form: two launches over tiles of the plane ----
+// A block owns kN1TileX x kN1TileY nodes (threads along x) and walks tiles
+// gridDim.y apart along y.  The strain launch evaluates S and |grad s| on the
+// tile and a two-node halo into shared memory and takes the fourth
+// differences there; the filter launch runs the x pass on the tile's columns
+// and a two-row halo, then the y pass with the coefficients.  Halo positions
+// take the values of the node the row-mapped stencils read there: x wrapped
+// on a periodic x, clamped to the nearest interior node otherwise; y wrapped.
+// The arithmetic of every value is that of the per-node stages above.
+constexpr int kN1TileX = 128, kN1TileY = 16;
+constexpr int kN1HX = kN1TileX + 4, kN1HY = kN1TileY + 4;
+
+// x of the node whose values a stencil reads at x (any integer)
+__device__ __forceinline__ int n1_xsrc(const Params& p, int x) {
+  return p.periodic_x ? modp(x, p.Nx) : (x < 0 ? 0 : (x >= p.Nx ? p.Nx - 1 : x));
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kN1TileX)
+k_n1_strain_d4_2d(Params p, const real* __restrict__ rho, const real* __restrict__ u, const real* __restrict__ T) {
+  __shared__ real sv[2][kN1HY][kN1HX];             // S, |grad s| on the tile and its halo
+  const N1Buffers<2, real> b(p, rho, u, T);
+  const unsigned pitch = unsigned(p.pitch);
+  const int x0 = blockIdx.x * kN1TileX, tx = threadIdx.x;
+  const int ntile = (p.Ny + kN1TileY - 1) / kN1TileY;
+  for (int ty = blockIdx.y; ty < ntile; ty += gridDim.y) {
+    const int y0 = ty * kN1TileY;
+#pragma unroll 4
+    for (int k = tx; k < kN1HX * kN1HY; k += kN1TileX) {
+      const int hx = k % kN1HX, hy = k / kN1HX;
+      const int xs = n1_xsrc(p, x0 + hx - 2), ys = modp(y0 + hy - 2, p.Ny);
+      const N1Vals<real, 2> v =
+          n1_strain_at<2, real>(p, b.rho, b.u, b.T, xs, ys, 0, unsigned(ys) * pitch + unsigned(xs + p.G));
+      sv[0][hy][hx] = v.v[0];
+      sv[1][hy][hx] = v.v[1];
+    }
+    __syncthreads();
+    const int x = x0 + tx, hx = tx + 2;
+    if (x < p.Nx) {
+      for (int r = 0; r < kN1TileY && y0 + r < p.Ny; ++r) {
+        const int hy = r + 2;
+        N1Vals<real, 2> res;
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const real(*v)[kN1HX] = sv[f];
+          real acc = real(0);                        // axis x, then y (n1_d4_at)
+          const real dx = n1_fourth(v[hy][hx - 2], v[hy][hx - 1], v[hy][hx], v[hy][hx + 1], v[hy][hx + 2]);
+          acc += dx * dx;
+          const real dy = n1_fourth(v[hy - 2][hx], v[hy - 1][hx], v[hy][hx], v[hy + 1][hx], v[hy + 2][hx]);
+          acc += dy * dy;
+          res.v[f] = sqrt(acc);
+        }
+        n1_store(p, b.w1, unsigned(y0 + r) * pitch + unsigned(x + p.G), res);
+      }
+    }
+    __syncthreads();                                 // the next tile overwrites sv
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kN1TileX)
+k_n1_filter_coef_2d(Params p, const real* __restrict__ rho, const real* __restrict__ T) {
+  __shared__ real sf[2][kN1HY][kN1TileX];          // x-filtered norms; each thread reads only its own column
+  const N1Buffers<2, real> b(p, rho, nullptr, T);
+  const Model<real> m = model_of<real>(p);
+  const unsigned pitch = unsigned(p.pitch);
+  const int tx = threadIdx.x, x = blockIdx.x * kN1TileX + tx;
+  if (x >= p.Nx) return;
+  const int ntile = (p.Ny + kN1TileY - 1) / kN1TileY;
+  for (int ty = blockIdx.y; ty < ntile; ty += gridDim.y) {
+    const int y0 = ty * kN1TileY;
+#pragma unroll 4
+    for (int hy = 0; hy < kN1HY; ++hy) {
+      const int ys = modp(y0 + hy - 2, p.Ny);
+      const N1Vals<real, 2> v = n1_filter_at<real>(p, 0, b.w1, x, ys, 0, unsigned(ys) * pitch + unsigned(x + p.G));
+      sf[0][hy][tx] = v.v[0];
+      sf[1][hy][tx] = v.v[1];
+    }
+    for (int r = 0; r < kN1TileY && y0 + r < p.Ny; ++r) {
+      const int hy = r + 2;
+      // y pass, then the coefficients (as n1_filter_coef_at)
+      const real s4 =
+          n1_binom5(sf[0][hy - 2][tx], sf[0][hy - 1][tx], sf[0][hy][tx], sf[0][hy + 1][tx], sf[0][hy + 2][tx]);
+      const real g4 =
+          n1_binom5(sf[1][hy - 2][tx], sf[1][hy - 1][tx], sf[1][hy][tx], sf[1][hy + 1][tx], sf[1][hy + 2][tx]);
+      const unsigned o = unsigned(y0 + r) * pitch + unsigned(x + p.G);
+      n1_store(p, b.visc, o, n1_coefs(p, m, n1_ld(b.rho + o), n1_ld(b.T + o), s4, g4));
+    }
+  }
+}
+
 // The whole update of a handle's coefficients from the step's rho, u (D planes),
-// T (padded plane layout): D + 2 launches.
+// T (padded plane layout): 2 launches in 2-D, D + 2 in 3-D.
 template <int D, typename real>
 inline int n1_update(const Params& p, cudaStream_t st, const real* rho, const real* u, const real* T) {
-  const int groups = (p.Ny * p.Nz + kN1Rows - 1) / kN1Rows;
-  const dim3 block(128), grid(unsigned((p.Nx + 127) / 128), unsigned(groups < 65535 ? groups : 65535));
-  k_n1_strain<D, real><<<grid, block, 0, st>>>(p, rho, u, T);
-  k_n1_d4<D, real><<<grid, block, 0, st>>>(p);
-  for (int a = 0; a + 1 < D; ++a) k_n1_filter<D, real><<<grid, block, 0, st>>>(p, a);
-  k_n1_filter_coef<D, real><<<grid, block, 0, st>>>(p, rho, T);
-  return D + 2;
+  if constexpr (D == 2) {
+    const int ntile = (p.Ny + kN1TileY - 1) / kN1TileY;
+    const dim3 grid(unsigned((p.Nx + kN1TileX - 1) / kN1TileX), unsigned(ntile < 65535 ? ntile : 65535));
+    k_n1_strain_d4_2d<real><<<grid, kN1TileX, 0, st>>>(p, rho, u, T);
+    k_n1_filter_coef_2d<real><<<grid, kN1TileX, 0, st>>>(p, rho, T);
+    return 2;
+  } else {
+    const int groups = (p.Ny * p.Nz + kN1Rows - 1) / kN1Rows;
+    const dim3 block(128), grid(unsigned((p.Nx + 127) / 128), unsigned(groups < 65535 ? groups : 65535));
+    k_n1_strain<D, real><<<grid, block, 0, st>>>(p, rho, u, T);
+    k_n1_d4<D, real><<<grid, block, 0, st>>>(p);
+    for (int a = 0; a + 1 < D; ++a) k_n1_filter<D, real><<<grid, block, 0, st>>>(p, a);
+    k_n1_filter_coef<D, real><<<grid, block, 0, st>>>(p, rho, T);
+    return D + 2;
+  }
 }
 
 // ---- batched kernels: one block per row of every instance with shock capturing ----
