@@ -4,14 +4,16 @@
 //
 //   {mu, eta}^num = rho C_{mu,eta} F(|grad^4 S|),  k^num = rho c_s C_k F(|grad^4 |grad s||)
 //
-// with S = |grad u + grad u^T| / 2, grad s = (c_v/T) grad T - R/(rho (1 - b rho)) grad rho,
-// |grad^4 f| = sqrt(sum_a (d_a^4 f)^2) over the per-axis five-point fourth
-// differences (r = 5, delta x^(r+1) = 1), F the separable binomial filter
-// (1, 4, 6, 4, 1)/16 along every axis, c_s the van der Waals sound speed
-// at (rho, T).  Neighbours wrap on periodic axes and are clamped to the
-// nearest interior node on non-periodic x faces.  Fields live on the padded
-// plane layout of the handle (offset (z Ny + y) pitch + x + G, one plane per
-// component); threads along x, blocks over x and the rows.
+// with S = |grad u + grad u^T| / 2, grad s = (c_v/T) grad T - R/(rho (1 - b rho)) grad rho
+// (van der Waals; the general identity for Peng-Robinson), |grad^4 f| =
+// sqrt(sum_a (d_a^4 f)^2) over the per-axis five-point fourth differences
+// (r = 5, delta x^(r+1) = 1), F the separable binomial filter (1, 4, 6, 4, 1)/16
+// along every axis, c_s the fluid's sound speed at (rho, T).  Neighbours wrap
+// on periodic axes and are clamped to the nearest interior node on
+// non-periodic x faces.  Fields live on the padded plane layout of the handle
+// (offset (z Ny + y) pitch + x + G, one plane per component).  Three forms
+// share the per-node arithmetic: 2-D tiles in shared memory (two launches),
+// row-mapped launches in 3-D (D + 2), and one block per row for batches.
 #pragma once
 
 #include "lbm_fused.cuh"
