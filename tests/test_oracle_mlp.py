@@ -91,6 +91,73 @@ def test_adamw_first_step_is_signed_lr():
     assert np.allclose(th, 1.0 - 0.1 * 0.5)
 
 
+def xphi(z):
+    """z Phi(z): the GELU that the tanh form approximates within 5e-4 (pinned above)."""
+    return z * 0.5 * (1.0 + math.erf(z / math.sqrt(2.0)))
+
+
+def sparse_network():
+    """Parameters with a few non-zero entries, so the outputs follow by hand.
+    Layer 1: unit 0 sees x_0, unit 5 sees -x_1 + 0.25.  Layer 2: unit 3 sees h1_0,
+    unit 7 sees 2 h1_5 - 0.5.  Outputs: y_0 = h2_3, y_1 = 0.1 - h2_7, y_2 = 0.3."""
+    p = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+    p["W1"][0, 0] = 1.0
+    p["W1"][5, 1], p["b1"][5] = -1.0, 0.25
+    p["W2"][3, 0] = 1.0
+    p["W2"][7, 5], p["b2"][7] = 2.0, -0.5
+    p["W3"][0, 3] = 1.0
+    p["W3"][1, 7], p["b3"][1] = -1.0, 0.1
+    p["b3"][2] = 0.3
+    return mlp.pack(p)
+
+
+SPARSE_X = np.array([[0.7, -0.4], [-1.2, 0.9], [1.5, -1.1]])
+
+
+def forward_wiring_error():
+    """Largest deviation of mlp.forward on the sparse network from the hand composition."""
+    y, _ = mlp.forward(sparse_network(), SPARSE_X)
+    err = 0.0
+    for (x0, x1), out in zip(SPARSE_X, y):
+        want = (xphi(xphi(x0)), 0.1 - xphi(2.0 * xphi(0.25 - x1) - 0.5), 0.3)
+        err = max(err, float(np.abs(out - np.array(want)).max()))
+    return err
+
+
+def test_forward_wiring_of_a_sparse_network():
+    assert forward_wiring_error() < 3e-3          # the tanh GELU's own deviation, through two layers
+
+
+def loss_normalisation_error():
+    """The loss of outputs offset by (c_0, c_1, c_2) is (c_0^2 + c_1^2 + c_2^2)/3, whatever n."""
+    theta = sparse_network()
+    y, _ = mlp.forward(theta, SPARSE_X)
+    c = np.array([0.2, -0.5, 0.1])
+    loss, _ = mlp.loss_and_grad(theta, SPARSE_X, y - c)
+    return abs(loss / (np.sum(c * c) / 3.0) - 1.0)
+
+
+def test_loss_is_the_mean_square_over_samples_and_outputs():
+    assert loss_normalisation_error() < 1e-12
+
+
+def adamw_constant_gradient_error(steps=25):
+    """With a constant gradient g the bias-corrected moments are g and g^2 at every t,
+    so each step moves theta by lr g/(|g| + eps) (Kingma & Ba; wd = 0)."""
+    g = np.array([0.3, -2.0, 1e-3])
+    th, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    err = 0.0
+    for t in range(1, steps + 1):
+        th, m, v = mlp.adamw_step(th, g, m, v, t, lr=0.01)
+        want = -0.01 * t * g / (np.abs(g) + 1e-8)
+        err = max(err, float(np.abs(th / want - 1.0).max()))
+    return err
+
+
+def test_adamw_bias_correction_keeps_constant_gradient_steps_equal():
+    assert adamw_constant_gradient_error() < 1e-9
+
+
 def test_targets_are_the_oracle_closure():
     rho = np.array([0.3, 0.6, 0.9]); T = np.array([0.09, 0.15, 0.12])
     a, b, R, cv = 0.25, 1 / 3, 8 / 3, 8.0

@@ -222,3 +222,57 @@ def test_flipped_density_term_of_entropy_gradient_breaks_isentrope_pin(monkeypat
     monkeypatch.setattr(lbm, "entropy_gradient_magnitude", flipped)
     with pytest.raises(AssertionError):
         n1.test_entropy_gradient_of_isothermal_ramp_and_isentrope()
+
+
+# ---- learned closure oracle (oracle/mlp.py) ----
+
+def test_transposed_hidden_weights_break_wiring_pin(monkeypatch):
+    import test_oracle_mlp as tm
+    from oracle import mlp
+    orig_unpack = mlp.unpack
+
+    def unpack_t(theta):
+        p = orig_unpack(theta)
+        p["W2"] = p["W2"].T.copy()
+        return p
+    monkeypatch.setattr(mlp, "unpack", unpack_t)
+    assert tm.forward_wiring_error() > 0.05
+
+
+def test_hidden_bias_dropped_breaks_wiring_pin(monkeypatch):
+    import test_oracle_mlp as tm
+    from oracle import mlp
+    orig_unpack = mlp.unpack
+
+    def unpack_nob(theta):
+        p = orig_unpack(theta)
+        p["b2"] = 0.0 * p["b2"]
+        return p
+    monkeypatch.setattr(mlp, "unpack", unpack_nob)
+    assert tm.forward_wiring_error() > 0.05
+
+
+def test_loss_summed_over_outputs_breaks_normalisation_pin(monkeypatch):
+    import test_oracle_mlp as tm
+    from oracle import mlp
+    orig = mlp.loss_and_grad
+
+    def summed(theta, X, Y):
+        loss, g = orig(theta, X, Y)
+        return 3.0 * loss, 3.0 * g
+    monkeypatch.setattr(mlp, "loss_and_grad", summed)
+    assert tm.loss_normalisation_error() > 0.5
+
+
+def test_adamw_without_second_moment_correction_breaks_constant_gradient_pin(monkeypatch):
+    import test_oracle_mlp as tm
+    from oracle import mlp
+
+    def adamw_nov(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+        m = beta1 * m + (1 - beta1) * grad
+        v = beta2 * v + (1 - beta2) * grad * grad
+        mhat = m / (1 - beta1 ** t)
+        theta = theta - lr * (mhat / (np.sqrt(v) + eps) + wd * theta)
+        return theta, m, v
+    monkeypatch.setattr(mlp, "adamw_step", adamw_nov)
+    assert tm.adamw_constant_gradient_error() > 0.1
