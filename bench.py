@@ -97,7 +97,6 @@ BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 MAX_CHUNK = {("tgv", "fp32"): 200, ("tgv", "fp16dev"): 100, ("tgv", "fp64"): 400, ("strong_shock", "fp32"): 500,
              ("shock_column", "fp32"): 1500, ("batch_columns", "fp32"): 400}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16dev": "f16-storage/f32"}
-KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_fused.cuh", "lbm_mlp.cuh", "lbm_capi.cu"]
 
 
 def build_case(name):
@@ -106,13 +105,23 @@ def build_case(name):
     return getattr(inputs, builder)(**kw), prec, desc
 
 
+def kernel_sources():
+    """Every file the library is built from: all of csrc/, the public headers and the build script."""
+    pkg = os.path.join(ROOT, "paper_2510_14712_gb300")
+    src = os.path.join(pkg, "csrc")
+    inc = os.path.join(ROOT, "include")
+    files = [os.path.join(src, f) for f in sorted(os.listdir(src))]
+    files += [os.path.join(inc, f) for f in sorted(os.listdir(inc))]
+    return files + [os.path.join(pkg, "build.py")]
+
+
 def kernel_hash():
-    """Hash of the sources and build flags of the step kernels (traffic counters
-    in profiles/traffic.json are used only while it matches)."""
+    """Hash of the sources and build flags of the library (traffic counters in
+    profiles/traffic.json are used only while it matches)."""
     h = hashlib.sha256()
-    src = os.path.join(ROOT, "paper_2510_14712_gb300", "csrc")
-    for p in [os.path.join(src, f) for f in KERNEL_SOURCES] + [os.path.join(ROOT, "paper_2510_14712_gb300", "build.py")]:
-        if os.path.exists(p):
+    for p in kernel_sources():
+        if os.path.isfile(p):
+            h.update(os.path.basename(p).encode())
             h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
@@ -200,26 +209,93 @@ def replica_mlups(nodes, steps, world, seconds):
     return nodes * steps * world / seconds / 1e6
 
 
-def cpu_oracle_leg(workload, seconds=15.0, steps=None, warmup=1):
-    """Time the FP64 oracle on a bounded sample of the workload (runs in a child process)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import bench, json; print(json.dumps(bench._oracle_sample(%r, %r, %r, %r)))"
-            % (workload, seconds, steps, warmup))
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
-    if r.returncode != 0:
-        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr else "oracle leg failed"}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def _oracle_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
 
 
-def _oracle_sample(workload, seconds, steps=None, warmup=1):
-    """Oracle MLUPS on a sub-box of the workload: same physics, fewer nodes, few steps.
+def cpu_model():
+    """CPU model name of the host (lscpu / /proc/cpuinfo), or the machine type."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
-    With ``steps`` given, exactly that many timed steps after ``warmup``;
-    otherwise as many as fit in ``seconds`` (at most 1000).
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _run_children(codes, timeout=600):
+    procs = [subprocess.Popen([sys.executable, "-c", c], cwd=ROOT, env=_oracle_env(), stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for c in codes]
+    outs = []
+    for p in procs:
+        try:
+            o, e = p.communicate(timeout=timeout)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            o, e = p.communicate()
+        if p.returncode != 0:
+            return None, (e.strip().splitlines()[-1] if e else "oracle leg failed")
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    return outs, None
+
+
+def cpu_oracle_leg(workload, seconds=12.0, steps=None, warmup=1, save=None, all_cores=True):
+    """Time the FP64 oracle on a bounded sample of the workload in child processes.
+
+    One process on one core (as many steps as fit in ``seconds``, or ``steps``),
+    saving its final fields to ``save`` when given; then, with ``all_cores``, one
+    process per host core, each stepping its own copy of the sample the same
+    number of steps from a common start time.  ``value`` is the all-core
+    figure: the node updates of every process over the common wall time.
     """
-    import numpy as np
+    code = ("import bench, json; print(json.dumps(bench._oracle_sample(%r, %r, %r, %r, save=%r)))"
+            % (workload, seconds, steps, warmup, save))
+    outs, err = _run_children([code])
+    if err:
+        return {"error": err}
+    one = outs[0]
+    res = {"value": one["value"], "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": one["sample"],
+           "model": cpu_model(), "single_core": {"value": one["value"], "sample": one["sample"]}}
+    if not all_cores:
+        return res
+    n = host_cores()
+    k = one["steps"]
+    t_start = time.time() + 3.0 + 0.05 * n          # every child has imported and built its case by then
+    codes = ["import bench, json; print(json.dumps(bench._oracle_sample(%r, None, %r, %r, start_at=%r)))"
+             % (workload, k, warmup, t_start) for _ in range(n)]
+    outs, err = _run_children(codes)
+    if err:
+        res["all_cores_error"] = err
+        return res
+    wall = max(o["t_end"] for o in outs) - t_start
+    late = max(o["t_begin"] for o in outs) - t_start
+    updates = sum(o["nodes"] * o["steps"] for o in outs)
+    res.update(value=updates / wall / 1e6, cores=n,
+               sample="%s; %d processes (one per core, %s), %d steps each, common wall time %.1f s "
+                      "(last start %.2f s after the common start)" % (one["sample_case"], n, res["model"], k, wall,
+                                                                        late))
+    return res
+
+
+def _sample_case(workload):
+    """The bounded oracle sample of a workload: (case, description)."""
     import inputs
-    from oracle import lbm as olbm
     builder, kw, prec, _ = WORKLOADS[workload]
     if builder == "tgv":
         case = inputs.tgv(shape=(48, 48, 48), scenario_name=kw.get("scenario_name", "tgv_d3q27"))
@@ -249,24 +325,73 @@ def _oracle_sample(workload, seconds, steps=None, warmup=1):
     else:
         case = inputs.shock_column(3, (128, 64, 64), radius=8, center=(32, 32, 32), shock_x=16)
         sample = "D3Q27 shock-liquid sphere 128x64x64 down-scale (radius 8) with shock capturing, FP64 oracle"
+    return case, sample
+
+
+def _oracle_sample(workload, seconds, steps=None, warmup=1, save=None, start_at=None):
+    """Oracle MLUPS on a sub-box of the workload: same physics, fewer nodes, few steps.
+
+    With ``steps`` given, exactly that many timed steps after ``warmup``;
+    otherwise as many as fit in ``seconds`` (at most 1000).  ``start_at``: a
+    time.time() to wait for before the timed steps.  ``save``: an .npz path for
+    the final rho, u, T (and the total step count).
+    """
+    import numpy as np
+    from oracle import lbm as olbm
+    case, sample = _sample_case(workload)
     m = olbm.Model(case.D, case.shape, case.eos, case.tau, case.Pr, case.cv, case.x_low, case.x_high)
     m.shock_capturing = SC_WORKLOADS.get(workload)
     s = olbm.Sim(m, case.rho, case.u, case.T)
     s.step(warmup)
-    done, t0 = 0, time.perf_counter()
+    if start_at is not None:
+        time.sleep(max(0.0, start_at - time.time()))
+    done, t_begin = 0, time.time()
+    t0 = time.perf_counter()
     while True:
         s.step(1)
         done += 1
         el = time.perf_counter() - t0
         if (steps is not None and done >= steps) or (steps is None and (el > seconds or done >= 1000)):
             break
+    t_end = time.time()
     n = int(np.prod(case.shape))
-    return {"value": n * done / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    if save:
+        F = s.fields()
+        np.savez(save, rho=F["rho"], u=np.stack(F["u"]), T=F["T"], steps=warmup + done)
+    return {"value": n * done / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle", "nodes": n, "steps": done,
+            "t_begin": t_begin, "t_end": t_end, "sample_case": sample,
             "sample": "%s, %d steps, %.1f s, 1 thread" % (sample, done, el)}
 
 
+def l2_vs_oracle(P, workload, prec, path, t64=False):
+    """Relative L2 error of the GPU path against the oracle's final fields of the CPU
+    leg (same sample box, same steps, the line's precision)."""
+    import numpy as np
+    if not path or not os.path.exists(path):
+        return None
+    ref = np.load(path)
+    steps = int(ref["steps"])
+    case, sample = _sample_case(workload)
+    s = P.Solver(case, precision=prec, t_fp64=t64)
+    try:
+        sc = SC_WORKLOADS.get(workload)
+        if sc:
+            P.lbm_set_shock_capturing(s.h, *sc)
+        s.init().step(steps)
+        got = s.fields()
+    finally:
+        s.close()
+    err = {}
+    for k in ("rho", "u", "T"):
+        a, b = np.asarray(got[k]), np.asarray(ref[k])
+        err[k] = float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    err.update(steps=steps, box="x".join(str(v) for v in case.shape), against="FP64 CPU oracle",
+               closure="exact", sample=sample.replace(", FP64 oracle", ""))
+    return err
+
+
 def run_reference(args):
-    """The FP64 oracle on the host cores: W warm-up and K timed steps of the bounded sample."""
+    """The FP64 oracle on all host cores: W warm-up and K timed steps of the bounded sample per core."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -279,9 +404,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "impl": "FP64 CPU oracle (numpy), bounded sample"},
+            "config": {"workload": desc, "impl": "FP64 CPU oracle (numpy), bounded sample, one process per host core"},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "model": r.get("model"), "single_core": r.get("single_core")},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -347,7 +472,14 @@ def run_batched(args):
                          "algorithmic_bytes_per_step": alg, "peak_source": peak_kind},
             "e2e": None, "gpu_launches": launches}
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_leg(args.workload)
+        import tempfile
+        path = os.path.join(tempfile.gettempdir(), "lbm_oracle_%d.npz" % os.getpid())
+        line["cpu_baseline"] = cpu_oracle_leg(args.workload, save=path)
+        try:
+            line["l2_error"] = l2_vs_oracle(P, args.workload, prec, path)
+        finally:
+            if os.path.exists(path):
+                os.unlink(path)
     print(json.dumps(line))
     return 0
 
@@ -378,7 +510,8 @@ def run_ours(args):
     N = case.nodes
     stream = torch.cuda.current_stream(dev)
     sk = P.LBM_STEP_MULTIPASS if args.step_kernel == "multipass" else P.LBM_STEP_FUSED
-    solver = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
+    t64 = args.t64
+    solver = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk, t_fp64=t64)
     sc_coef = SC_WORKLOADS.get(args.workload)
     if sc_coef:
         P.lbm_set_shock_capturing(solver.h, *sc_coef)
@@ -475,7 +608,7 @@ def run_ours(args):
         o_rho, o_u, o_T = torch.empty_like(h_rho).pin_memory(), torch.empty_like(h_u).pin_memory(), \
             torch.empty_like(h_T).pin_memory()
         tot = np.empty(case.D + 2)
-        s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk)
+        s2 = P.Solver(case, precision=prec, stream=stream.cuda_stream, step_kernel=sk, t_fp64=t64)
         if sc_coef:
             P.lbm_set_shock_capturing(s2.h, *sc_coef)
         if net is not None:
@@ -513,6 +646,7 @@ def run_ours(args):
                        "tile_shape": tile[0] if tile else None, "tile_candidates_ms": tile_ms,
                        "timed_chunk_steps": min(chunk, args.steps), "cuda_graphs": bool(args.graphs),
                        "shock_capturing": list(sc_coef) if sc_coef else None,
+                       "temperature_inversion": ("fp64" if t64 else "fp32") if prec != "fp64" else "fp64",
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)" % (2 * Q * BYTES[prec] * N / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -526,7 +660,16 @@ def run_ours(args):
             closure_info["gain_vs_exact"] = value / world / closure_info["exact_closure_mlups"]
             line["closure"] = closure_info
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_oracle_leg(args.workload)
+            # the oracle on the host cores; its single-core run's final fields give the
+            # line's stated error: the same sample box on the GPU, same steps, the line's precision
+            import tempfile
+            path = os.path.join(tempfile.gettempdir(), "lbm_oracle_%d.npz" % os.getpid())
+            line["cpu_baseline"] = cpu_oracle_leg(args.workload, save=path)
+            try:
+                line["l2_error"] = l2_vs_oracle(P, args.workload, prec, path, t64)
+            finally:
+                if os.path.exists(path):
+                    os.unlink(path)
         print(json.dumps(line))
     if net is not None:
         net.close()
@@ -570,6 +713,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--t64", action="store_true",
+                    help="FP64 temperature inversion in the FP32 / FP16-deviation kernels "
+                         "(lbm_set_temperature_fp64; default: the whole step in FP32)")
     ap.add_argument("--graphs", action="store_true",
                     help="replay captured CUDA graphs (lbm_set_graphs); each chunk is timed as a whole")
     ap.add_argument("--train-steps", type=int, default=None,

@@ -275,6 +275,27 @@ int lbm_autotune_times(lbm_t h, float* ms_per_step, int n);
  * Returns the count (>= 1), or LBM_EINVAL for a NULL handle. */
 int lbm_tile_count(lbm_t h);
 
+/* Mixed-precision form of the FP32 and FP16-deviation handles (FP32
+ * collision, FP64 kept for the temperature inversion).  With `on` the
+ * temperature of Eq. lbm_temp, T = (E - |u|^2/2 + a rho) / c_v, is evaluated
+ * in FP64 from the FP32 moments E = (S + u.F/2)/rho and u, and rounded once to
+ * FP32; for the Peng-Robinson fluid (Sec. 2: T from the non-linear caloric
+ * relation) e = E - |u|^2/2 and the root's argument e - B0 are formed in FP64.
+ * Off (the default): the whole step in FP32.  The FP64 form costs about 6% of
+ * the 256^3 D3Q27 step.  Its effect on the error against the FP64 oracle
+ * depends on the flow: on Ma 1.2 shock tubes it lowers it (T about threefold),
+ * on a drifting Taylor-Green vortex it raises it (rho about twofold); the
+ * trajectory error of FP32 runs is set by rounding throughout the step, not
+ * by the inversion alone.  FP64 handles ignore the setting (their arithmetic
+ * is FP64), and so do the learned closure (its network replaces the
+ * inversion) and the batched step (FP32 inversion).  Applies to the fused
+ * and multi-pass steps from the next step on; does not synchronise.
+ * Errors: LBM_EINVAL (NULL handle). */
+int lbm_set_temperature_fp64(lbm_t h, int on);
+/* 1 while the FP64 temperature inversion is in use (FP32 / FP16-deviation
+ * handles with it switched on), else 0 (also for a NULL handle). */
+int lbm_get_temperature_fp64(lbm_t h);
+
 /* Use tile shape `index` (0 <= index < lbm_tile_count(h); 0 is the default)
  * for the fused step from now on, instead of the autotuner's choice.  Every
  * shape computes the same step.  The setting lasts until the next lbm_init,
@@ -363,6 +384,11 @@ const char* lbm_batch_last_error(void);
  * calls on a device share the array, which keeps the last call's contents;
  * every call overwrites all the partials it reads, so nothing needs
  * clearing, but calls that overlap on the GPU race and give wrong totals.
+ * The looked-up address is kept for the life of the process: after
+ * cudaDeviceReset (or any teardown of the device's primary context) it is
+ * stale, and the entry point must not be called again in that process.
+ * An error left pending by earlier, unrelated CUDA work is cleared before
+ * the launches, so that a launch failure reported here is this call's own.
  * Errors: LBM_EINVAL (bad lattice, NULL pointer, n out of range), LBM_ECUDA;
  * the message is returned by lbm_totals_noalloc_error(). */
 int lbm_totals_noalloc(int lattice, long long n, const double* d_rho, const double* d_u, const double* d_T,

@@ -33,7 +33,7 @@ EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_
            "lbm_step", "lbm_step_async", "lbm_sync", "lbm_moments", "lbm_moments_device",
            "lbm_get_flags", "lbm_population_bytes", "lbm_get_populations", "lbm_set_populations",
            "lbm_set_step_kernel", "lbm_autotune", "lbm_autotune_times", "lbm_tile_count", "lbm_set_tile",
-           "lbm_set_graphs",
+           "lbm_set_graphs", "lbm_set_temperature_fp64", "lbm_get_temperature_fp64",
            "lbm_set_shock_capturing", "lbm_launch_count",
            "lbm_destroy",
            "lbm_last_error", "lbm_version",
@@ -99,6 +99,8 @@ def load():
         "lbm_tile_count": (I, [P]),
         "lbm_set_tile": (I, [P, I]),
         "lbm_set_graphs": (I, [P, I]),
+        "lbm_set_temperature_fp64": (I, [P, I]),
+        "lbm_get_temperature_fp64": (I, [P]),
         "lbm_set_shock_capturing": (I, [P, D, D, D]),
         "lbm_launch_count": (ctypes.c_longlong, [P]),
         "lbm_destroy": (I, [P]),
@@ -287,6 +289,15 @@ def lbm_set_shock_capturing(h, C_mu=0.1, C_eta=0.0, C_k=0.1):
 
 def lbm_set_graphs(h, on=True):
     _check(load().lbm_set_graphs(h, 1 if on else 0))
+
+
+def lbm_set_temperature_fp64(h, on=True):
+    """FP64 temperature inversion in the FP32 / FP16-deviation kernels (default off)."""
+    _check(load().lbm_set_temperature_fp64(h, 1 if on else 0))
+
+
+def lbm_get_temperature_fp64(h):
+    return bool(load().lbm_get_temperature_fp64(h))
 
 
 def lbm_tile_count(h):
@@ -525,7 +536,9 @@ def lbm_mlp_destroy(net):
 class Solver:
     """One handle set up from an ``inputs.Case``-like description."""
 
-    def __init__(self, case, precision="fp64", stream=None, step_kernel=LBM_STEP_FUSED):
+    def __init__(self, case, precision="fp64", stream=None, step_kernel=LBM_STEP_FUSED, t_fp64=None):
+        """t_fp64: FP64 temperature inversion of the FP32 / FP16-deviation kernels
+        (None keeps the library default, off)."""
         self.case = case
         self.D = case.D
         Nx, Ny = case.shape[0], case.shape[1]
@@ -535,6 +548,8 @@ class Solver:
         if stream:
             lbm_set_stream(self.h, stream)
         lbm_set_step_kernel(self.h, step_kernel)
+        if t_fp64 is not None:
+            lbm_set_temperature_fp64(self.h, t_fp64)
         for face, spec in ((LBM_FACE_XLO, case.x_low), (LBM_FACE_XHI, case.x_high)):
             if spec == "periodic":
                 continue

@@ -1,0 +1,13 @@
+// Fused step with the FP64 temperature inversion (exact van der Waals
+// closure): D = 2, storage float, arithmetic float.
+#include "lbm_ops.cuh"
+
+namespace lbm {
+void step_d2_fp32_t64(Handle& h, const void* src, void* dst) {
+  OpsImpl<2, float, float>::step_cl<ExactClosure<float, true>>(h, src, dst);
+}
+int autotune_d2_fp32_t64(Handle& h, int reps, float* best_ms) {
+  return OpsImpl<2, float, float>::autotune_cl<ExactClosure<float, true>>(h, reps, best_ms);
+}
+int ntiles_d2_fp32_t64() { return OpsImpl<2, float, float>::ntiles_cl<ExactClosure<float, true>>(); }
+}  // namespace lbm

@@ -1,5 +1,5 @@
 // Fused step with the exact Peng-Robinson closure: D = 3, FP32 and FP64 storage
-// and arithmetic.
+// and arithmetic, FP32 also with the FP64 temperature inversion.
 #include "lbm_ops.cuh"
 
 namespace lbm {
@@ -17,4 +17,11 @@ int autotune_d3_fp64_pr(Handle& h, int reps, float* best_ms) {
   return OpsImpl<3, double, double>::autotune_cl<PrClosure<double>>(h, reps, best_ms);
 }
 int ntiles_d3_fp64_pr() { return OpsImpl<3, double, double>::ntiles_cl<PrClosure<double>>(); }
+void step_d3_fp32_pr_t64(Handle& h, const void* src, void* dst) {
+  OpsImpl<3, float, float>::step_cl<PrClosure<float, true>>(h, src, dst);
+}
+int autotune_d3_fp32_pr_t64(Handle& h, int reps, float* best_ms) {
+  return OpsImpl<3, float, float>::autotune_cl<PrClosure<float, true>>(h, reps, best_ms);
+}
+int ntiles_d3_fp32_pr_t64() { return OpsImpl<3, float, float>::ntiles_cl<PrClosure<float, true>>(); }
 }  // namespace lbm

@@ -225,9 +225,18 @@ int lbm_batch_autotune(lbm_batch_t b, int reps, int* chosen, float* ms_per_step)
   for (int k = 0; k < b->n; ++k)
     if (!b->inst[k]->initialized) return bfail(LBM_ESTATE, "instance " + std::to_string(k) + " not initialised");
   const int ncfg = bops(*b)->batch_ncfg();
-  cudaEvent_t e0, e1;
-  BCK(cudaEventCreate(&e0));
-  BCK(cudaEventCreate(&e1));
+  // the timing events and the tuning mode are released on every return path
+  struct Guard {
+    lbm::Batch* b;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Guard() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      b->tuning = 0;
+    }
+  } g{b};
+  BCK(cudaEventCreate(&g.e0));
+  BCK(cudaEventCreate(&g.e1));
   int best = 0;
   float bt = 1e30f;
   b->tuning = 1;                                             // tile shapes only change the fused step
@@ -235,24 +244,19 @@ int lbm_batch_autotune(lbm_batch_t b, int reps, int* chosen, float* ms_per_step)
     b->tile_cfg = c;
     b->graph_ready = 0;
     int rc = ready(*b);
-    if (rc != LBM_OK) {
-      b->tuning = 0;
-      return rc;
-    }
+    if (rc != LBM_OK) return rc;
     BCK(cudaGraphLaunch(b->graph[b->cur], b->stream));      // warm-up; writes the spare buffers only
-    BCK(cudaEventRecord(e0, b->stream));
+    BCK(cudaEventRecord(g.e0, b->stream));
     for (int r = 0; r < reps; ++r) BCK(cudaGraphLaunch(b->graph[b->cur], b->stream));
-    BCK(cudaEventRecord(e1, b->stream));
-    BCK(cudaEventSynchronize(e1));
+    BCK(cudaEventRecord(g.e1, b->stream));
+    BCK(cudaEventSynchronize(g.e1));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, g.e0, g.e1);
     if (ms < bt) {
       bt = ms;
       best = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   b->tuning = 0;
   b->tile_cfg = best;
   b->graph_ready = 0;

@@ -70,19 +70,42 @@ Ops with_pr(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tu
   return o;
 }
 
+// Exact-closure table with the fused step and the autotuner of the FP64
+// temperature inversion (the multi-pass step reads Params::t64; batches keep
+// the FP32 inversion).
+Ops with_t64(const Ops* base, void (*step)(Handle&, const void*, void*), int (*tune)(Handle&, int, float*),
+             int (*ntiles)()) {
+  Ops o = *base;
+  o.step = step;
+  o.autotune = tune;
+  o.ntiles = ntiles;
+  return o;
+}
+
 const Ops* ops_for(const Handle& h) {
   if (h.p.eos_kind == LBM_EOS_PR) {
     static const Ops p2f = with_pr(ops_d2_fp32(), step_d2_fp32_pr, autotune_d2_fp32_pr, ntiles_d2_fp32_pr);
     static const Ops p3f = with_pr(ops_d3_fp32(), step_d3_fp32_pr, autotune_d3_fp32_pr, ntiles_d3_fp32_pr);
     static const Ops p2d = with_pr(ops_d2_fp64(), step_d2_fp64_pr, autotune_d2_fp64_pr, ntiles_d2_fp64_pr);
     static const Ops p3d = with_pr(ops_d3_fp64(), step_d3_fp64_pr, autotune_d3_fp64_pr, ntiles_d3_fp64_pr);
+    static const Ops p2t = with_pr(ops_d2_fp32(), step_d2_fp32_pr_t64, autotune_d2_fp32_pr_t64, ntiles_d2_fp32_pr_t64);
+    static const Ops p3t = with_pr(ops_d3_fp32(), step_d3_fp32_pr_t64, autotune_d3_fp32_pr_t64, ntiles_d3_fp32_pr_t64);
     if (h.precision == LBM_FP64) return h.D == 2 ? &p2d : &p3d;
+    if (h.t64) return h.D == 2 ? &p2t : &p3t;
     return h.D == 2 ? &p2f : &p3f;
   }
   if (h.closure == LBM_CLOSURE_MLP) {
     static const Ops m2 = with_mlp(ops_d2_fp32(), step_d2_fp32_mlp, autotune_d2_fp32_mlp, ntiles_d2_fp32_mlp);
     static const Ops m3 = with_mlp(ops_d3_fp32(), step_d3_fp32_mlp, autotune_d3_fp32_mlp, ntiles_d3_fp32_mlp);
     return h.D == 2 ? &m2 : &m3;
+  }
+  if (h.t64 && h.precision != LBM_FP64) {
+    static const Ops t2f = with_t64(ops_d2_fp32(), step_d2_fp32_t64, autotune_d2_fp32_t64, ntiles_d2_fp32_t64);
+    static const Ops t3f = with_t64(ops_d3_fp32(), step_d3_fp32_t64, autotune_d3_fp32_t64, ntiles_d3_fp32_t64);
+    static const Ops t2h = with_t64(ops_d2_fp16(), step_d2_fp16_t64, autotune_d2_fp16_t64, ntiles_d2_fp16_t64);
+    static const Ops t3h = with_t64(ops_d3_fp16(), step_d3_fp16_t64, autotune_d3_fp16_t64, ntiles_d3_fp16_t64);
+    if (h.precision == LBM_FP32) return h.D == 2 ? &t2f : &t3f;
+    return h.D == 2 ? &t2h : &t3h;
   }
   if (h.D == 2) {
     if (h.precision == LBM_FP64) return ops_d2_fp64();
@@ -298,6 +321,8 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
   p.eos_kind = eos->kind;
   p.Tc = eos->kind == LBM_EOS_PR ? eos->Tc : 0.0;
   p.mpr = eos->kind == LBM_EOS_PR ? eos->m : 0.0;
+  // the FP64 temperature inversion of the FP32 kernels is off until switched on
+  h->t64 = p.t64 = 0;
   Model<double> m = host_model(*h);
   const double P_ref = eos_pressure(m, eos->rho_ref, eos->T_ref);
   if (!(P_ref > 0)) {
@@ -591,6 +616,15 @@ int lbm_set_shock_capturing(lbm_t h, double C_mu, double C_eta, double C_k) {
   }
   return LBM_OK;
 }
+
+int lbm_set_temperature_fp64(lbm_t h, int on) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  h->t64 = (on && h->precision != LBM_FP64) ? 1 : 0;   // FP64 arithmetic inverts in FP64 anyway
+  h->p.t64 = h->t64;                                    // step graphs are re-captured (they record Params)
+  return LBM_OK;
+}
+
+int lbm_get_temperature_fp64(lbm_t h) { return h ? h->t64 : 0; }
 
 int lbm_set_graphs(lbm_t h, int on) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");

@@ -57,6 +57,18 @@ template <typename real> struct Model {
   real Tc, mpr;              // Peng-Robinson: T_c and the slope m of sqrt(alpha) in sqrt(T/T_c)
 };
 
+// The FP64 temperature inversion of Eq. lbm_temp used by the FP32 kernels when
+// it is switched on (lbm_set_temperature_fp64): T = (E - |u|^2/2 + a rho) / c_v
+// evaluated in FP64 from the FP32 moments, rounded once to FP32.  Returns T;
+// e = E - |u|^2/2 (the specific internal energy) is rounded into `e`.  Most of
+// FP32's error in T comes from E - |u|^2/2, so the subtraction is the part
+// that needs the wider type, not only the division.
+__host__ __device__ inline float vdw_temperature_fp64(double a, double inv_cv, float rho, float E, float u2, float& e) {
+  const double ed = double(E) - 0.5 * double(u2);
+  e = float(ed);
+  return float((ed + a * double(rho)) * inv_cv);
+}
+
 template <typename real> __host__ __device__ inline real vdw_pressure(const Model<real>& m, real rho, real T) {
   return rho * m.R * T / (real(1) - m.b * rho) - m.a * rho * rho;          // Eq. Pvdw
 }
@@ -118,6 +130,19 @@ template <typename real> __host__ __device__ inline real pr_temperature(const Mo
   const real q = e - B0;
   const real y = real(2) * q / (A + sqrt(A * A + real(4) * m.cv * q));
   return y * y;
+}
+// The same root with e given in FP64 (the FP64 temperature inversion of the
+// FP32 kernels): q = e - B0 is formed in FP64 and rounded once; the root of
+// positive terms is then evaluated in FP32.
+__host__ __device__ inline float pr_temperature_q(const Model<float>& m, float rho, double e) {
+  const float c = pr_c(m, rho), k = m.mpr;
+  const float A = m.a * c * (1.0f + k) * k / sqrtf(m.Tc), B0 = -m.a * c * (1.0f + k) * (1.0f + k);
+  const float q = float(e - double(B0));
+  const float y = 2.0f * q / (A + sqrtf(A * A + 4.0f * m.cv * q));
+  return y * y;
+}
+__host__ __device__ inline double pr_temperature_q(const Model<double>& m, double rho, double e) {
+  return pr_temperature(m, rho, e);
 }
 
 // ---- the fluid of a handle (Model::kind): van der Waals or Peng-Robinson ----
@@ -293,7 +318,16 @@ template <int D, typename real> struct Attractors {
       fe *= pe[a][L::c(I, a)];
       fs *= pf[a][L::c(I, a)];
     }
-    return f + twobeta * (fe - f) + omb * (fs - fe);
+    return relax(f, fe, fs - fe);
+  }
+
+  // p + 2 beta (p^eq - p) + (1 - beta) d, d = p^* - p^eq: the form of Eqs.
+  // fLBGK / gLBGK whose terms are differences of nearly equal populations, so
+  // that each rounding is relative to a small quantity (expanding it into
+  // (1 - 2 beta) p + (3 beta - 1) p^eq + (1 - beta) p^* rounds three terms of
+  // the size of p and, near beta = 1, cancels two of them)
+  __device__ __forceinline__ real relax(real p, real pe_, real d) const {
+    return fma(omb, d, fma(twobeta, pe_ - p, p));
   }
 
   // g_i + 2 beta (g_i^eq - g_i) + (1 - beta)(g_i^* - g_i^eq)      (Eq. gLBGK)
@@ -329,7 +363,7 @@ template <int D, typename real> struct Attractors {
       cq += real(L::c(I, a)) * qc[a];
     }
     if (nz == 1) gs += real(0.5) * cq;                                     // Eq. LBMgstar, |c_i|^2 = 1
-    return g + twobeta * (ge - g) + omb * (gs - ge);
+    return relax(g, ge, gs - ge);
   }
 };
 
@@ -338,7 +372,7 @@ template <int D, typename real> struct Attractors {
 // axes ("lower" axes: x, and y in 3-D); for each group the products over the
 // lower axes are formed once and the three directions of the group differ
 // only in the factor of the last axis.  The update of Eqs. fLBGK / gLBGK is
-// written as (1 - 2 beta) p + (3 beta - 1) p^eq + (1 - beta) p^*.
+// Attractors::relax of p, p^eq and p^* - p^eq.
 // load(i) / store(i, v) move population i.
 template <int D, typename real> struct FactoredRelax {
   using L = Lattice<D>;
@@ -346,7 +380,6 @@ template <int D, typename real> struct FactoredRelax {
 
   template <class Load, class Store>
   __device__ __forceinline__ static void f_pass(const Attractors<D, real>& at, Load load, Store store) {
-    const real k0 = real(1) - at.twobeta, k1 = real(1.5) * at.twobeta - real(1), k2 = at.omb;
 #pragma unroll
     for (int gi = 0; gi < NG; ++gi) {
       const int cx = D == 3 ? gi / 3 - 1 : gi - 1;
@@ -359,16 +392,16 @@ template <int D, typename real> struct FactoredRelax {
 #pragma unroll
       for (int cl = -1; cl <= 1; ++cl) {
         const int i = 3 * gi + cl + 1;
-        const real fe = fe2 * at.pe[D - 1][cl], fs = fs2 * at.pf[D - 1][cl];
+        const real fe = fe2 * at.pe[D - 1][cl];
+        const real d = fma(fs2, at.pf[D - 1][cl], -fe);                   // f^* - f^eq, one rounding
         const real f = load(i);
-        store(i, k0 * f + k1 * fe + k2 * fs);
+        store(i, at.relax(f, fe, d));
       }
     }
   }
 
   template <class Load, class Store>
   __device__ __forceinline__ static void g_pass(const Attractors<D, real>& at, Load load, Store store) {
-    const real k0 = real(1) - at.twobeta, k1 = real(1.5) * at.twobeta - real(1), k2 = at.omb;
 #pragma unroll
     for (int gi = 0; gi < NG; ++gi) {
       const int cx = D == 3 ? gi / 3 - 1 : gi - 1;
@@ -389,14 +422,15 @@ template <int D, typename real> struct FactoredRelax {
       for (int cl = -1; cl <= 1; ++cl) {
         const int i = 3 * gi + cl + 1;
         const real ge = at.pe[D - 1][cl] * Ce + Ae * at.ce[D - 1][cl];      // Eq. LBMeqG
-        real gs = at.pg[D - 1][cl] * Cs + As * at.cg[D - 1][cl];            // Eq. LBMgstar
+        // g^* - g^eq (Eq. LBMgstar) with g^* accumulated onto -g^eq
+        real d = fma(at.pg[D - 1][cl], Cs, fma(As, at.cg[D - 1][cl], -ge));
         if (nzl + (cl != 0) == 1) {                                          // |c_i|^2 = 1
           const real cq = cl != 0 ? real(cl) * at.qc[D - 1]
                                   : (cx != 0 ? real(cx) * at.qc[0] : real(cy) * at.qc[D == 3 ? 1 : 0]);
-          gs += real(0.5) * cq;
+          d += real(0.5) * cq;
         }
         const real g = load(i);
-        store(i, k0 * g + k1 * ge + k2 * gs);
+        store(i, at.relax(g, ge, d));
       }
     }
   }

@@ -54,21 +54,37 @@ template <int D, int TX, int TY, int EX = 0> struct FusedGeom {
   }
 };
 
-// Thermodynamic closures (rho, e) -> (T, P, c_s^2) used by stage C of the
-// fused step.  kWarp: the closure is warp-collective (every lane calls it,
+// Thermodynamic closures used by stage C of the fused step: from rho, the
+// specific total energy E and |u|^2 they give e = E - |u|^2/2 and
+// (T, P, c_s^2).  kWarp: the closure is warp-collective (every lane calls it,
 // `act` says whether the lane's node is real).  kExtra: fields the closure
 // adds to the primitive ring.  kSmem: shared-memory table bytes it loads.
+// load() runs once per CTA before the first work item.
 
-// Exact van der Waals closure: Eqs. lbm_temp (with e = E - u^2/2), Pvdw,
-// vdW_speed_of_sound.
-template <typename real> struct ExactClosure {
+// Exact van der Waals closure: Eqs. lbm_temp, Pvdw, vdW_speed_of_sound.
+// T64 (FP32 arithmetic only): the temperature inversion of Eq. lbm_temp in
+// FP64 (vdw_temperature_fp64), the mixed-precision form of the FP32 and
+// FP16-deviation builds.
+template <typename real, bool T64 = false> struct ExactClosure {
+  static constexpr bool kPr = false;
   static constexpr bool kWarp = false;
   static constexpr int kExtra = 0;
   static constexpr size_t kSmem = 0;
-  __device__ __forceinline__ void load(const Params&, unsigned char*) {}
-  __device__ __forceinline__ void operator()(const Model<real>& m, real rho, real e, bool, real& T, real& P,
-                                             real& cs2) const {
-    T = (e + m.a * rho) / m.cv;
+  double a64 = 0.0, inv_cv64 = 0.0;
+  __device__ __forceinline__ void load(const Params& p, unsigned char*) {
+    if constexpr (T64) {
+      a64 = p.a;
+      inv_cv64 = 1.0 / p.cv;
+    }
+  }
+  __device__ __forceinline__ void operator()(const Model<real>& m, real rho, real E, real u2, bool, real& T, real& P,
+                                             real& cs2, real& e) const {
+    if constexpr (T64 && sizeof(real) == 4) {
+      T = vdw_temperature_fp64(a64, inv_cv64, rho, E, u2, e);
+    } else {
+      e = E - real(0.5) * u2;
+      T = (e + m.a * rho) / m.cv;
+    }
     P = vdw_pressure(m, rho, T);
     cs2 = vdw_cs2(m, rho, T);
   }
@@ -76,15 +92,25 @@ template <typename real> struct ExactClosure {
 
 // Exact Peng-Robinson closure: T from the quadratic in sqrt(T) of its caloric
 // relation, then P and c_s^2 of the fluid; stage D reads P and c_s^2 from the
-// centre ring (kExtra = 2) and e = h - P/rho.
-template <typename real> struct PrClosure {
+// centre ring (kExtra = 2) and e = h - P/rho.  T64 (FP32 arithmetic only):
+// e = E - |u|^2/2 and the root's argument e - B0 in FP64, rounded once; the
+// root itself has only positive terms and stays in FP32.
+template <typename real, bool T64 = false> struct PrClosure {
+  static constexpr bool kPr = true;
   static constexpr bool kWarp = false;
   static constexpr int kExtra = 2;
   static constexpr size_t kSmem = 0;
   __device__ __forceinline__ void load(const Params&, unsigned char*) {}
-  __device__ __forceinline__ void operator()(const Model<real>& m, real rho, real e, bool, real& T, real& P,
-                                             real& cs2) const {
-    T = pr_temperature(m, rho, e);
+  __device__ __forceinline__ void operator()(const Model<real>& m, real rho, real E, real u2, bool, real& T, real& P,
+                                             real& cs2, real& e) const {
+    if constexpr (T64 && sizeof(real) == 4) {
+      const double ed = double(E) - 0.5 * double(u2);
+      e = real(ed);
+      T = pr_temperature_q(m, rho, ed);
+    } else {
+      e = E - real(0.5) * u2;
+      T = pr_temperature(m, rho, e);
+    }
     P = pr_pressure(m, rho, T);
     cs2 = pr_cs2(m, rho, T);
   }
@@ -93,6 +119,7 @@ template <typename real> struct PrClosure {
 // Learned closure: the network of lbm_mlp.cuh inside its training box, the
 // exact closure outside it (range gate).  FP32 arithmetic only.
 struct MlpClosure {
+  static constexpr bool kPr = false;
   static constexpr bool kWarp = true;
   static constexpr int kExtra = 2;
   static constexpr size_t kSmem = sizeof(mlp::Image);
@@ -102,8 +129,9 @@ struct MlpClosure {
     mlp::load_image(static_cast<const mlp::Image*>(p.mlp), d);
     w = d;
   }
-  __device__ __forceinline__ void operator()(const Model<float>& m, float rho, float e, bool act, float& T, float& P,
-                                             float& cs2) const {
+  __device__ __forceinline__ void operator()(const Model<float>& m, float rho, float E, float u2, bool act, float& T,
+                                             float& P, float& cs2, float& e) const {
+    e = E - 0.5f * u2;
     mlp::closure_warp(*w, m, rho, e, act, T, P, cs2);
   }
 };
@@ -128,14 +156,15 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
 }
 
 // One (column, z-segment) work item of the fused step: all planes mb..me-1 of
-// the TX x TY column at (x0, y0), reading A and writing B.  Shared by the
-// single-instance kernel and the batched persistent kernel.  SMALL: the box
-// is narrower than a tile plus its halo in x or y, so coordinates need an
-// exact modulo instead of a single conditional wrap.
+// the column of TX x hy nodes at (x0, y0) (hy <= TY rows; 1 in 2-D), reading A
+// and writing B.  Shared by the single-instance kernel and the batched
+// persistent kernel.  SMALL: the box is narrower than a tile plus its halo in
+// x or y, so coordinates need an exact modulo instead of a single conditional
+// wrap.
 template <int D, typename S, typename real, int TX, int TY, bool SMALL, class CL>
 __device__ __forceinline__ void fused_column(const Params& p, const typename Store<S>::T* __restrict__ A,
-                                             typename Store<S>::T* __restrict__ B, int x0, int y0, int mb, int me,
-                                             unsigned char* smem_raw, unsigned& flags, const CL& closure) {
+                                             typename Store<S>::T* __restrict__ B, int x0, int y0, int hy, int mb,
+                                             int me, unsigned char* smem_raw, unsigned& flags, const CL& closure) {
   using L = Lattice<D>;
   using G = FusedGeom<D, TX, TY, CL::kExtra>;
   constexpr int Q = L::Q;
@@ -156,6 +185,11 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   using ST = typename Store<S>::T;
   // element offsets inside a population buffer fit 32 bits (checked at create)
   const unsigned plane32 = unsigned(p.plane), pitch32 = unsigned(p.pitch);
+  // stage A by quads of four x nodes (vector loads): x rows of 4-aligned
+  // quads, i.e. a periodic x of a multiple of 4 nodes (quads wrap whole) at
+  // least a tile plus two quads wide, or ghost-padded x (quad starts at padded
+  // multiples of 4; pitch >= Nx + 8 keeps every needed quad in its row)
+  const bool vec = !SMALL && TX % 4 == 0 && (!p.periodic_x || (p.Nx % 4 == 0 && p.Nx >= TX + 8));
 
   for (int pl = mb - 3; pl <= me + 2; ++pl) {
     // ---------------- A: moments of plane pl --------------------------------
@@ -175,7 +209,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
       auto moments = [&](const int k) {
         const int lx = k % G::BX3, ly = k / G::BX3;
-        const int ox = outside(lx, 3, TX), oy = D == 3 ? outside(ly, G::HY3, TY) : 0;
+        const int ox = outside(lx, 3, TX), oy = D == 3 ? outside(ly, G::HY3, hy) : 0;
         const int gx = x0 + lx - 3;
         if (ox + oy > 3 || gx < xmin || gx > xmax) return;
         const bool in1 = ox + oy <= 1;
@@ -232,10 +266,127 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           dst[D * G::N1] = Se;
         }
       };
-      constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
+      if (vec && !wtile) {
+        // Quads of four x nodes: tasks are (row, quad) of the R3 box for f
+        // (rho, and j on R1) and of the R1 box for g (S).  Per direction one
+        // vector load covers the quad's sources for c_x = 0; the sources of
+        // c_x = +1 (x - 1) and -1 (x + 1) are shifted by one node, and the one
+        // outside the quad is a scalar load, made only when that node is
+        // needed.  Each node sums its populations in the direction order of
+        // the scalar path, so both give bitwise the same moments.
+        constexpr int NQ = TX / 4 + 2;                            // quads per row: x0 - 4 .. x0 + TX + 3
+        constexpr int NF = NQ * G::BY3, NTASK = NQ * (G::BY3 + G::BY1);
 #pragma unroll 1
-      for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
-      if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
+        for (int t = tid; t < NTASK; t += G::NT) {
+          const bool isg = t >= NF;
+          const int tt = isg ? t - NF : t;
+          const int qx = tt % NQ;
+          const int ly = isg ? tt / NQ + (G::HY3 - G::HY1) : tt / NQ;   // row of the R3 box
+          const int oy = D == 3 ? outside(ly, G::HY3, hy) : 0;
+          const int lim = isg ? 1 : 3;
+          if (oy > lim) continue;
+          const int xq = x0 - 4 + 4 * qx;                         // interior x of the quad's first node
+          bool need[4], in1[4];
+          bool any = false;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int ox = outside(xq + k - x0 + 3, 3, TX);
+            need[k] = ox + oy <= lim && xq + k >= xmin && xq + k <= xmax;
+            in1[k] = need[k] && ox + oy <= 1;
+            any = any || need[k];
+          }
+          if (!any) continue;
+          const int gy = D == 3 ? wrapc<false>(y0 + ly - G::HY3, p.Ny) : 0;
+          unsigned yr[3];
+#pragma unroll
+          for (int c = -1; c <= 1; ++c) yr[c + 1] = D == 3 ? unsigned(wrapc<false>(gy - c, p.Ny)) * pitch32 : 0u;
+          const unsigned xq0 = unsigned(p.periodic_x ? wrapc<false>(xq, p.Nx) : xq + p.G);
+          const unsigned xqm = unsigned(p.periodic_x ? wrapc<false>(xq - 1, p.Nx) : xq + p.G - 1);
+          const unsigned xq4 = unsigned(p.periodic_x ? wrapc<false>(xq + 4, p.Nx) : xq + p.G + 4);
+          const int lx0 = xq - x0 + 3;                            // R3-box x of the quad's first node
+          // The directions in three groups of c_x = g - 1 (i = g Q/3 + j), a rolled
+          // loop so that one group's loads are in flight at a time (all 27
+          // vector loads at once would not fit the register budget); within a
+          // group j fixes the other components.  Every accumulation chain still
+          // runs in increasing i.
+          // pulled values of the quad's four nodes for direction i = g Q/3 + j of kind f (off 0) or g (off Q)
+          auto pulled = [&](const int g, const int j, const int off, real* w) {
+            constexpr int J = Q / 3;
+            const int i = g * J + j;
+            const int cy = D == 3 ? j / 3 - 1 : 0, cm = D == 3 ? j % 3 - 1 : j - 1;
+            const ST* row = Pm[cm + 1] + (unsigned(off + i) * plane32 + yr[cy + 1]);
+            real v[4];
+            Store<S>::template ld4<real>(row, xq0, p.ref[off + i], v);
+            if (g == 1) {
+              w[0] = v[0]; w[1] = v[1]; w[2] = v[2]; w[3] = v[3];
+            } else if (g == 2) {                                  // c_x = +1: node x pulls from x - 1
+              w[0] = need[0] ? Store<S>::template ld<real>(row, xqm, p.ref[off + i]) : real(0);
+              w[1] = v[0]; w[2] = v[1]; w[3] = v[2];
+            } else {                                              // c_x = -1: node x pulls from x + 1
+              w[0] = v[1]; w[1] = v[2]; w[2] = v[3];
+              w[3] = need[3] ? Store<S>::template ld<real>(row, xq4, p.ref[off + i]) : real(0);
+            }
+          };
+          if (!isg) {
+            real rho[4], sp[4][D], sn[4][D];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              rho[k] = real(0);
+#pragma unroll
+              for (int a = 0; a < D; ++a) sp[k][a] = sn[k][a] = real(0);
+            }
+#pragma unroll 1
+            for (int g = 0; g < 3; ++g) {
+#pragma unroll
+              for (int j = 0; j < Q / 3; ++j) {
+                real w[4];
+                pulled(g, j, 0, w);
+                const int c1 = D == 3 ? j / 3 - 1 : j - 1, c2 = D == 3 ? j % 3 - 1 : 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  rho[k] += w[k];
+                  if (g == 2) sp[k][0] += w[k];
+                  if (g == 0) sn[k][0] += w[k];
+                  if (c1 == 1) sp[k][1] += w[k];
+                  if (c1 == -1) sn[k][1] += w[k];
+                  if (D == 3 && c2 == 1) sp[k][D - 1] += w[k];
+                  if (D == 3 && c2 == -1) sn[k][D - 1] += w[k];
+                }
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (need[k]) s_rho[slot * G::N3 + ly * G::BX3 + lx0 + k] = rho[k];
+              if (in1[k]) {
+                real* dst = s_mom + (slot * G::NMOM) * G::N1 + (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx0 + k - 2);
+#pragma unroll
+                for (int a = 0; a < D; ++a) dst[a * G::N1] = sp[k][a] - sn[k][a];
+              }
+            }
+          } else {
+            real Se[4] = {real(0), real(0), real(0), real(0)};
+#pragma unroll 1
+            for (int g = 0; g < 3; ++g) {
+#pragma unroll
+              for (int j = 0; j < Q / 3; ++j) {
+                real w[4];
+                pulled(g, j, Q, w);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Se[k] += w[k];
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (in1[k])
+                s_mom[(slot * G::NMOM + D) * G::N1 + (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx0 + k - 2)] = Se[k];
+          }
+        }
+      } else {
+        constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
+#pragma unroll 1
+        for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
+        if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
+      }
     }
     __syncthreads();
 
@@ -245,7 +396,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
       for (int k = tid; k < G::N2; k += G::NT) {
         const int lx = k % G::BX2, ly = k / G::BX2;
-        const int ox = outside(lx, 2, TX), oy = D == 3 ? outside(ly, G::HY2, TY) : 0;
+        const int ox = outside(lx, 2, TX), oy = D == 3 ? outside(ly, G::HY2, hy) : 0;
         if (ox + oy > 2) continue;
         const int gx = x0 + lx - 2;
         if (gx < xmin + 1 || gx > xmax - 1) continue;
@@ -269,10 +420,10 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       for (int k0 = tid - lane; k0 < G::N1; k0 += G::NT) {
         const int k = k0 + lane;
         const int lx = k % G::BX1, ly = k / G::BX1;
-        const int ox = outside(lx, 1, TX), oy = D == 3 ? outside(ly, G::HY1, TY) : 0;
+        const int ox = outside(lx, 1, TX), oy = D == 3 ? outside(ly, G::HY1, hy) : 0;
         const int gx = x0 + lx - 1;
         const bool act = k < G::N1 && ox + oy <= 1 && gx >= xmin + 2 && gx <= xmax - 2;
-        real rho = real(1), e = real(0), F[D], u[D];
+        real rho = real(1), E = real(0), u2 = real(0), F[D], u[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) F[a] = u[a] = real(0);
         if (act) {
@@ -285,20 +436,19 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           if (D == 3) F[1] = m.kappa * rho * real(0.5) * (lp[k2 + G::BX2] - lp[k2 - G::BX2]);
           F[D - 1] = m.kappa * rho * real(0.5) * (s_lap[sp * G::N2 + k2] - s_lap[sm * G::N2 + k2]);
           const real* mo = s_mom + (sc * G::NMOM) * G::N1 + k;
-          real uF = 0, u2 = 0;
+          real uF = 0;
 #pragma unroll
           for (int a = 0; a < D; ++a) {
             u[a] = (mo[a * G::N1] + real(0.5) * F[a]) / rho;                                   // Eq. def_u
             uF += u[a] * F[a];
             u2 += u[a] * u[a];
           }
-          const real E = (mo[D * G::N1] + real(0.5) * uF) / rho;                              // Eq. def_E
-          e = E - real(0.5) * u2;
+          E = (mo[D * G::N1] + real(0.5) * uF) / rho;                                         // Eq. def_E
         }
-        // closure (rho, e) -> (T, P, c_s^2)
-        real T = real(0), P = real(1), cs2 = real(0);
-        if constexpr (CL::kWarp) closure(m, rho, e, act, T, P, cs2);
-        else if (act) closure(m, rho, e, act, T, P, cs2);
+        // closure (rho, E, |u|^2) -> e, (T, P, c_s^2)
+        real T = real(0), P = real(1), cs2 = real(0), e = real(0);
+        if constexpr (CL::kWarp) closure(m, rho, E, u2, act, T, P, cs2, e);
+        else if (act) closure(m, rho, E, u2, act, T, P, cs2, e);
         if (act) {
           const real theta = P / rho;
           real* pr = s_prm + (sc * G::NPRIM) * G::N1 + k;
@@ -309,7 +459,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
             pr[(G::P_U + a) * G::N1] = u[a];
             pr[(G::P_LAM + a) * G::N1] = rho * u[a] * u[a] * u[a] + real(3) * rho * u[a] * (theta - real(1.0 / 3.0));
           }
-          if (lx >= 1 && lx <= TX && ly >= G::HY1 && ly < G::HY1 + TY) {                       // a tile node
+          if (lx >= 1 && lx <= TX && ly >= G::HY1 && ly < G::HY1 + hy) {                       // a tile node
             if (p.sc_on && q >= mb && q < me) {
               // this step's rho, u, T for the shock-capturing coefficients of the next step
               const int tx = x0 + lx - 1, ty = D == 3 ? y0 + ly - G::HY1 : 0;
@@ -344,7 +494,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
       const int lx = tid % TX, ly = tid / TX;
       const int gx = x0 + lx, gy = y0 + ly;
-      if (gx < p.Nx && (D == 2 || gy < p.Ny)) {
+      if (gx < p.Nx && (D == 2 || (ly < hy && gy < p.Ny))) {
         const int mq = modp(q, Nm);
         const ST* Pm[3];
         unsigned xc[3], yr[3];
@@ -437,7 +587,10 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 
 // Single-instance step: work items are (column, z-segment) pairs, ordered
 // segment-major so that the CTAs resident together cover neighbouring
-// columns at the same planes and their halos are L2 hits.  MINB: CTAs per SM
+// columns at the same planes and their halos are L2 hits.  Columns are TX
+// nodes wide and, in 3-D, one of ncoly bands of y rows (at most TY rows each;
+// the launch picks ncoly so that the columns spread evenly over the resident
+// CTA slots).  MINB: CTAs per SM
 // the register allocation must allow (2 keeps one CTA's memory phase
 // overlapping the other's collision).
 template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL, class CL = ExactClosure<real>>
@@ -446,10 +599,8 @@ k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __res
              typename Store<S>::T* __restrict__ B, unsigned* err, int ncolx, int ncoly, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CL closure;
-  if constexpr (CL::kSmem > 0) {
-    closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra>::template smem_bytes<real>());
-    __syncthreads();
-  }
+  closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra>::template smem_bytes<real>());
+  if constexpr (CL::kSmem > 0) __syncthreads();
   unsigned flags = 0;
   const int Nm = D == 3 ? p.Nz : p.Ny;
   const int ncol = ncolx * ncoly;
@@ -459,8 +610,11 @@ k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __res
     const int seg = int(it / ncol);
     const int mb = int((long long)Nm * seg / nseg), me = int((long long)Nm * (seg + 1) / nseg);
     const int x0 = (col % ncolx) * TX;
-    const int y0 = D == 3 ? (col / ncolx) * TY : 0;
-    fused_column<D, S, real, TX, TY, SMALL, CL>(p, A, B, x0, y0, mb, me, smem_raw, flags, closure);
+    // 3-D: ncoly bands of y rows, as even as integers allow (each at most TY rows)
+    const int band = col / ncolx;
+    const int y0 = D == 3 ? int((long long)p.Ny * band / ncoly) : 0;
+    const int hy = D == 3 ? int((long long)p.Ny * (band + 1) / ncoly) - y0 : 1;
+    fused_column<D, S, real, TX, TY, SMALL, CL>(p, A, B, x0, y0, hy, mb, me, smem_raw, flags, closure);
   }
   if (flags) atomicOr(err, flags);
 }
@@ -507,8 +661,8 @@ k_step_fused_batch(const BatchInstance* __restrict__ insts, const BatchItem* __r
     unsigned flags = 0;
     const bool small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
     const ExactClosure<real> cl{};
-    if (small) fused_column<D, S, real, TX, TY, true>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags, cl);
-    else fused_column<D, S, real, TX, TY, false>(p, A, B, x0, y0, w.mb, w.me, smem_raw, flags, cl);
+    if (small) fused_column<D, S, real, TX, TY, true>(p, A, B, x0, y0, TY, w.mb, w.me, smem_raw, flags, cl);
+    else fused_column<D, S, real, TX, TY, false>(p, A, B, x0, y0, TY, w.mb, w.me, smem_raw, flags, cl);
     if (flags) atomicOr(errs + w.inst, flags);
   }
 }

@@ -43,6 +43,9 @@ struct Params {
   double sc_c[3];
   void* sc_prims;
   const void* sc_visc;
+  // FP64 temperature inversion in FP32 arithmetic (lbm_set_temperature_fp64);
+  // read by the multi-pass step (the fused step selects its closure instead)
+  int t64;
 };
 
 template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
@@ -84,6 +87,7 @@ struct Handle {
   int use_graphs;             // lbm_set_graphs: replay captured two-step graphs
   void* graphs;               // StepGraphs (lbm_capi.cu), created on first use
   void* sc_buf;               // shock capturing: prims (D+2), visc (3), work (4) planes
+  int t64;                    // FP64 temperature inversion in the FP32 / FP16-deviation kernels
 };
 
 struct Batch;
@@ -167,5 +171,26 @@ int ntiles_d2_fp64_pr();
 int ntiles_d3_fp64_pr();
 int ntiles_d2_fp32_mlp();
 int ntiles_d3_fp32_mlp();
+// FP32 arithmetic with the FP64 temperature inversion (exact closures):
+// fused step, autotuner and tile count of FP32 and FP16-deviation storage,
+// van der Waals and Peng-Robinson
+void step_d2_fp32_t64(Handle& h, const void* src, void* dst);
+void step_d3_fp32_t64(Handle& h, const void* src, void* dst);
+void step_d2_fp16_t64(Handle& h, const void* src, void* dst);
+void step_d3_fp16_t64(Handle& h, const void* src, void* dst);
+void step_d2_fp32_pr_t64(Handle& h, const void* src, void* dst);
+void step_d3_fp32_pr_t64(Handle& h, const void* src, void* dst);
+int autotune_d2_fp32_t64(Handle& h, int reps, float* best_ms);
+int autotune_d3_fp32_t64(Handle& h, int reps, float* best_ms);
+int autotune_d2_fp16_t64(Handle& h, int reps, float* best_ms);
+int autotune_d3_fp16_t64(Handle& h, int reps, float* best_ms);
+int autotune_d2_fp32_pr_t64(Handle& h, int reps, float* best_ms);
+int autotune_d3_fp32_pr_t64(Handle& h, int reps, float* best_ms);
+int ntiles_d2_fp32_t64();
+int ntiles_d3_fp32_t64();
+int ntiles_d2_fp16_t64();
+int ntiles_d3_fp16_t64();
+int ntiles_d2_fp32_pr_t64();
+int ntiles_d3_fp32_pr_t64();
 
 }  // namespace lbm

@@ -12,7 +12,10 @@
 // The array is shared by every call on a device and keeps the contents of the
 // last call.  Each call writes every partial it reads, so nothing has to be
 // cleared first; but two calls that overlap on the GPU (different streams,
-// no ordering between them) race on it.
+// no ordering between them) race on it.  Its device address is looked up once
+// per device and kept for the life of the process: after cudaDeviceReset (or
+// any teardown of the device's primary context) the kept address is stale, so
+// a process that resets a device must not call this entry point again.
 #include <mutex>
 #include <string>
 
@@ -120,6 +123,10 @@ extern "C" int lbm_totals_noalloc(int lattice, long long n, const double* d_rho,
   double* partials = nullptr;
   int rc = scratch_for_current_device(&partials);
   if (rc != LBM_OK) return rc;
+  // an error left pending by earlier, unrelated work is taken off the error
+  // state here, so that the check after the launches sees this call's own
+  // launches only (a sticky error of a broken context fails them again)
+  const cudaError_t earlier = cudaGetLastError();
   const int nblocks = int((n + kNodesPerBlock - 1) / kNodesPerBlock);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (lattice == LBM_D2Q9) {
@@ -130,7 +137,11 @@ extern "C" int lbm_totals_noalloc(int lattice, long long n, const double* d_rho,
     k_field_totals_final<3><<<1, 32, 0, s>>>(partials, nblocks, d_totals);
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fail(LBM_ECUDA, std::string("launch: ") + cudaGetErrorString(e) +
+                               (earlier != cudaSuccess ? std::string(" (an earlier error was pending: ") +
+                                                             cudaGetErrorString(earlier) + ")"
+                                                       : std::string()));
   return LBM_OK;
 }
 

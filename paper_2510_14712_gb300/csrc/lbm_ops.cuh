@@ -49,9 +49,15 @@ template <int D, typename S, typename real> struct OpsImpl {
       int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
       bool small = false;
     };
-    // One CTA per (column, z-segment); enough segments to fill the resident
-    // CTA slots of the GPU, each at least 16 planes long (6 warm-up planes per
-    // segment), and never more items than slots so that all run together.
+    // One CTA per (column, z-segment), never more items than resident CTA
+    // slots so that all run together.  In 3-D the plane is cut into ncolx
+    // columns along x and ncoly bands along y (at least ceil(Ny / TY) bands,
+    // at most TY rows each); the number of bands and of z-segments (each at
+    // least 16 planes long: a segment repeats 6 warm-up planes) is the one that
+    // minimises the modelled time rounds x (rows per band + 1.5) x (planes per
+    // segment + 6): with 256 x 256 planes and 304 slots, 38 bands of 6-7 rows
+    // give every slot one column, where 32 bands of 8 rows would leave 48 slots
+    // without work.
     static Launch plan(const Params& p) {
       static int blocks_per_sm = -1, sms = 0;
       if (blocks_per_sm < 0) {
@@ -67,15 +73,27 @@ template <int D, typename S, typename real> struct OpsImpl {
       }
       Launch l;
       l.ncolx = (p.Nx + TX - 1) / TX;
-      l.ncoly = D == 3 ? (p.Ny + TY - 1) / TY : 1;
       const int Nm = D == 3 ? p.Nz : p.Ny;
-      const long long ncol = (long long)l.ncolx * l.ncoly;
       const long long slots = (long long)blocks_per_sm * sms;
-      long long nseg = slots / ncol;
-      if (nseg > Nm / 16) nseg = Nm / 16;
-      if (nseg < 1) nseg = 1;
-      l.nseg = int(nseg);
-      long long g = ncol * nseg;
+      const int nb0 = D == 3 ? (p.Ny + TY - 1) / TY : 1;
+      const int nb1 = D == 3 ? std::min(p.Ny, 2 * nb0) : 1;
+      double best = 1e300;
+      for (int nb = nb0; nb <= nb1; ++nb) {
+        const long long ncol = (long long)l.ncolx * nb;
+        long long nseg = slots / ncol;
+        if (nseg > Nm / 16) nseg = Nm / 16;
+        if (nseg < 1) nseg = 1;
+        const long long items = ncol * nseg;
+        const double rounds = double((items + slots - 1) / slots);
+        const double rows = D == 3 ? double((p.Ny + nb - 1) / nb) : 1.0;
+        const double cost = rounds * (rows + 1.5) * (double((Nm + nseg - 1) / nseg) + 6.0);
+        if (cost < best * (1.0 - 1e-9)) {
+          best = cost;
+          l.ncoly = nb;
+          l.nseg = int(nseg);
+        }
+      }
+      long long g = (long long)l.ncolx * l.ncoly * l.nseg;
       if (g > slots) g = slots;
       l.grid = int(g);
       l.small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
@@ -98,7 +116,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   // The learned closure adds a register-hungry network evaluation to stage C,
   // so its list also offers the unrestricted (MINB 1) allocation.
   template <class CL> static int candidates(const LaunchFn** fns) {
-    if constexpr (std::is_same<CL, PrClosure<real>>::value) {   // one shape: the Peng-Robinson sets compile fast
+    if constexpr (CL::kPr) {                                   // one shape: the Peng-Robinson sets compile fast
       static const LaunchFn c[] = {D == 3 ? &Fused<32, 8, sizeof(real) == 8 ? 1 : 2, CL>::launch
                                           : &Fused<256, 1, 2, CL>::launch};
       *fns = c;

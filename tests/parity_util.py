@@ -1,7 +1,24 @@
 """Helpers of the GPU parity tests: run one case on the oracle and on the CUDA path."""
+import json
+import os
+
 import numpy as np
 
 from oracle import lbm as olbm
+
+# Per-node bound of assert_parity, in units of the relative-L2 tolerance: the
+# largest |got - want| over the nodes may be at most node_mult * tol * rms(want).
+# A relative L2 bound over n nodes lets a single node be wrong by about
+# sqrt(n) * tol * rms(want) (100x tol on a 10^4-node box).  FP64 builds
+# (tolerances below 1e-9) get NODE_MULT: their largest node error is below
+# 0.4x tol on every parity case, so one wrong node at a tile seam, a wall
+# column or a wrapped edge fails.  FP32 builds get NODE_MULT_FP32: FP32
+# rounding can flip the side of Phi's upwind difference (Sec. 3.2) at isolated
+# nodes where a velocity component crosses zero (walls, stagnation points,
+# symmetry planes of the Taylor-Green vortex), a local jump of up to about
+# 25x tol x rms at a single node while the norm stays inside tol.
+NODE_MULT = 20.0
+NODE_MULT_FP32 = 50.0
 
 
 def oracle_run(case, steps):
@@ -12,9 +29,9 @@ def oracle_run(case, steps):
     return dict(rho=F["rho"], u=np.stack(F["u"]), T=F["T"], totals=s.totals())
 
 
-def gpu_run(case, steps, precision, chunk=None, step_kernel=0):
+def gpu_run(case, steps, precision, chunk=None, step_kernel=0, t_fp64=None):
     import paper_2510_14712_gb300 as P
-    s = P.Solver(case, precision=precision, step_kernel=step_kernel)
+    s = P.Solver(case, precision=precision, step_kernel=step_kernel, t_fp64=t_fp64)
     try:
         s.init()
         if chunk:
@@ -36,8 +53,38 @@ def rel_l2(a, b):
     return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
 
 
-def assert_parity(got, want, tol, what=""):
-    errs = {k: rel_l2(got[k], want[k]) for k in ("rho", "u", "T")}
-    bad = {k: v for k, v in errs.items() if not (v <= tol)}
-    assert not bad, "%s relative L2 above %g: %s" % (what, tol, errs)
-    return errs
+def node_err(a, b):
+    """Largest per-node |a - b| in units of rms(b), and the flat index of that node."""
+    d = np.abs(np.asarray(a) - np.asarray(b)).ravel()
+    rms = float(np.sqrt(np.mean(np.asarray(b, dtype=np.float64).ravel() ** 2)))
+    k = int(np.argmax(d)) if d.size else 0
+    return (float(d[k]) / rms if rms > 0 else float(d[k])), k
+
+
+def parity_errors(got, want, fields=("rho", "u", "T")):
+    """Relative L2 and per-node (max |got - want| / rms(want)) errors per field."""
+    l2 = {k: rel_l2(got[k], want[k]) for k in fields}
+    node = {k: node_err(got[k], want[k])[0] for k in fields}
+    return l2, node
+
+
+def _log(what, tol, l2, node):
+    path = os.environ.get("LBM_PARITY_LOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps(dict(what=what, tol=tol, l2=l2, node=node)) + "\n")
+
+
+def assert_parity(got, want, tol, what="", node_mult=None, fields=("rho", "u", "T")):
+    """Relative L2 of every field at most `tol`, and no single node off by more
+    than node_mult * tol * rms(want) (a wrong node at a tile seam, a wall
+    column or a wrapped edge cannot hide inside the norm)."""
+    if node_mult is None:
+        node_mult = NODE_MULT if tol < 1e-9 else NODE_MULT_FP32
+    l2, node = parity_errors(got, want, fields)
+    _log(what, tol, l2, node)
+    bad = {k: v for k, v in l2.items() if not (v <= tol)}
+    assert not bad, "%s relative L2 above %g: %s (per node %s)" % (what, tol, l2, node)
+    badn = {k: v for k, v in node.items() if not (v <= node_mult * tol)}
+    assert not badn, "%s per-node error above %g x %g x rms: %s (relative L2 %s)" % (what, node_mult, tol, node, l2)
+    return l2

@@ -26,7 +26,7 @@ def declared_symbols():
     for f in sorted(os.listdir(inc)):
         if f.endswith(".h"):
             src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
-            names.update(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src))
+            names.update(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
 

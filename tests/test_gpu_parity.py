@@ -127,6 +127,43 @@ def test_tgv_d3q27_fp32_long(tgv_long_ref):
     assert_parity(got, tgv_long_ref, 1e-5, "tgv fp32 1000 steps")
 
 
+# ---- the benchmark's own lattice parameters on a 64^3 box, 1000 steps ------------------
+# The 256^3 Taylor-Green workload's tau, U0, kappa and eta/mu (inputs.tgv(N=256):
+# tau is not rescaled to the smaller box), with the parity runs' seeded noise,
+# over 1000 steps: the tolerances of the FP64 (1e-12) and FP32 (1e-5) builds
+# and the 1e-3 density bound of FP16-deviation storage.
+
+def tgv_headline_case():
+    c = inputs.add_noise(inputs.tgv(shape=(64, 64, 64)), 0)     # the parity recipe's seeded 1e-3 noise
+    c.tau = inputs.scenario("tgv_d3q27")["tau"]
+    return c
+
+
+@pytest.fixture(scope="module")
+def tgv_headline_ref():
+    return oracle_run(tgv_headline_case(), 1000)
+
+
+def test_tgv_headline_params_64_fp64(tgv_headline_ref):
+    got = gpu_run(tgv_headline_case(), 1000, "fp64")
+    assert_parity(got, tgv_headline_ref, 1e-12, "tgv 64^3 (256^3 lattice parameters) fp64 1000 steps")
+
+
+def test_tgv_headline_params_64_fp32(tgv_headline_ref):
+    got = gpu_run(tgv_headline_case(), 1000, "fp32")
+    assert_parity(got, tgv_headline_ref, 1e-5, "tgv 64^3 (256^3 lattice parameters) fp32 1000 steps")
+
+
+def test_tgv_headline_params_64_fp32_multipass(tgv_headline_ref):
+    got = gpu_run(tgv_headline_case(), 1000, "fp32", step_kernel=P.LBM_STEP_MULTIPASS)
+    assert_parity(got, tgv_headline_ref, 1e-5, "tgv 64^3 (256^3 lattice parameters) fp32 multipass 1000 steps")
+
+
+def test_tgv_headline_params_64_fp16dev(tgv_headline_ref):
+    got = gpu_run(tgv_headline_case(), 1000, "fp16dev")
+    assert rel_l2(got["rho"], tgv_headline_ref["rho"]) <= 1e-3
+
+
 # ---- precision form: FP16 storage of deviations, FP32 collision ---------------------
 # The bound for this form is a relative L2 error of at most 1e-3 on rho
 # against the FP64 oracle; u and T are reported in the message.
@@ -424,3 +461,28 @@ def test_single_node_columns_and_ragged_tiles_fp64():
     ref = oracle_run(c, 12)
     got = gpu_run(c, 12, "fp64")
     assert_parity(got, ref, 1e-12, "ragged tgv fp64")
+
+
+# ---- precision form: FP64 temperature inversion in the FP32 kernels ----------------
+
+def test_temperature_fp64_switch():
+    """Off by default; can be switched on for FP32 / FP16-deviation handles, never for FP64 ones."""
+    c = inputs.tgv(shape=(8, 8, 8))
+    for prec in ("fp32", "fp16dev", "fp64"):
+        h = P.lbm_create(27, 8, 8, 8, c.eos, c.tau, c.Pr, c.cv, prec)
+        try:
+            assert not P.lbm_get_temperature_fp64(h)
+            P.lbm_set_temperature_fp64(h, False)
+            assert not P.lbm_get_temperature_fp64(h)
+            P.lbm_set_temperature_fp64(h, True)
+            assert P.lbm_get_temperature_fp64(h) == (prec != "fp64")
+        finally:
+            P.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("step_kernel", [0, 1])
+def test_tgv_headline_params_64_fp32_fp64_temperature(tgv_headline_ref, step_kernel):
+    """The mixed-precision form (FP64 temperature inversion), fused and multi-pass."""
+    got = gpu_run(tgv_headline_case(), 1000, "fp32", t_fp64=True, step_kernel=step_kernel)
+    assert_parity(got, tgv_headline_ref, 1e-5, "tgv 64^3 (256^3 lattice parameters) fp32 T64 %s 1000 steps"
+                  % ("multipass" if step_kernel else "fused"))
