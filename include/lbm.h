@@ -398,6 +398,21 @@ const char* lbm_totals_noalloc_error(void);
 /* Free all resources of the handle.  lbm_destroy(NULL) is a no-op. */
 int lbm_destroy(lbm_t h);
 
+/* Test hook for the out-of-memory paths: the k-th device allocation that the
+ * library makes from now on (counted over all handles and batches of the
+ * process) fails as cudaMalloc does when memory is exhausted, without
+ * allocating, so that the calling entry point returns LBM_ENOMEM after
+ * releasing what it had allocated; k = 0 disarms it.  Production code has no
+ * reason to call it.  Errors: LBM_EINVAL (k < 0). */
+int lbm_debug_fail_alloc(int k);
+
+/* Population accesses of the step kernels (fused, multi-pass, ghost fill,
+ * initialisation) that fell outside the handle's population buffers since the
+ * library was loaded, in a library built with -DLBM_BOUNDS_CHECK (each such
+ * access is skipped: a load gives 0, a store is dropped); -1 in other builds,
+ * which compile the checks away.  A test hook, like lbm_debug_fail_alloc. */
+long long lbm_debug_bounds_violations(void);
+
 /* Human-readable description of the last error on this thread. */
 const char* lbm_last_error(void);
 

@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+# LBM_LIBRARY selects another build of the library (the bounds-check build,
+# _build/liblbm_bc.so, of tests/test_gpu_bounds.py)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "_build", "liblbm.so")
 
 LBM_D2Q9, LBM_D3Q27 = 9, 27
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
@@ -36,7 +38,7 @@ EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_
            "lbm_set_graphs", "lbm_set_temperature_fp64", "lbm_get_temperature_fp64",
            "lbm_set_shock_capturing", "lbm_launch_count",
            "lbm_destroy",
-           "lbm_last_error", "lbm_version",
+           "lbm_last_error", "lbm_version", "lbm_debug_fail_alloc", "lbm_debug_bounds_violations",
            "lbm_totals_noalloc", "lbm_totals_noalloc_error",
            "lbm_batch_create", "lbm_batch_set_boundary", "lbm_batch_set_shock_capturing", "lbm_batch_set_stream",
            "lbm_batch_init",
@@ -106,6 +108,8 @@ def load():
         "lbm_destroy": (I, [P]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
+        "lbm_debug_fail_alloc": (I, [I]),
+        "lbm_debug_bounds_violations": (ctypes.c_longlong, []),
         "lbm_totals_noalloc": (I, [I, ctypes.c_longlong, P, P, P, D, D, P, P]),
         "lbm_totals_noalloc_error": (ctypes.c_char_p, []),
         "lbm_batch_create": (I, [ctypes.POINTER(P), I, I, P, P, P, ctypes.POINTER(lbm_eos), D, D, D]),
@@ -298,6 +302,16 @@ def lbm_set_temperature_fp64(h, on=True):
 
 def lbm_get_temperature_fp64(h):
     return bool(load().lbm_get_temperature_fp64(h))
+
+
+def lbm_debug_fail_alloc(k):
+    """Test hook: the k-th device allocation of the library from now on fails (0 disarms)."""
+    _check(load().lbm_debug_fail_alloc(int(k)))
+
+
+def lbm_debug_bounds_violations():
+    """Out-of-buffer population accesses so far (bounds-check builds; -1 otherwise)."""
+    return int(load().lbm_debug_bounds_violations())
 
 
 def lbm_tile_count(h):

@@ -2,7 +2,10 @@
 
 nvcc compiles each csrc/*.cu translation unit for sm_103a in parallel and
 links them into one shared library exporting the C interface of
-include/lbm.h.  Usage: ``python -m paper_2510_14712_gb300.build [--force]``.
+include/lbm.h.  Usage: ``python -m paper_2510_14712_gb300.build [--force]
+[--bounds-check]``.  The bounds-check build (-DLBM_BOUNDS_CHECK, every
+population access of the step kernels checked against its buffer) goes to
+_build/liblbm_bc.so with its own objects.
 """
 import concurrent.futures as cf
 import os
@@ -14,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
+LIB_BC = os.path.join(OUT, "liblbm_bc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-O3"]
@@ -39,25 +43,28 @@ def extra_flags(src):
     return []
 
 
-def _stale(srcs):
-    if not os.path.exists(LIB):
+def _stale(srcs, lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = srcs + [os.path.join(SRC, f) for f in os.listdir(SRC)] + \
         [os.path.join(HERE, "..", "include", f) for f in ("lbm.h", "lbm_mlp.h")] + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force=False, verbose=False):
+def build(force=False, verbose=False, bounds_check=False):
     srcs = sources()
-    if not force and not _stale(srcs):
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+    lib = LIB_BC if bounds_check else LIB
+    if not force and not _stale(srcs, lib):
+        return lib
+    objdir = os.path.join(OUT, "bc") if bounds_check else OUT
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
+    defs = ["-DLBM_BOUNDS_CHECK"] if bounds_check else []
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + ARCH + FLAGS + extra_flags(src) + ["-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc] + ARCH + FLAGS + defs + extra_flags(src) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -67,14 +74,14 @@ def build(force=False, verbose=False):
 
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds_check="--bounds-check" in sys.argv))

@@ -117,8 +117,8 @@ int lbm_batch_create(lbm_batch_t* out, int lattice, int n, const int* Nx, const 
     b->inst[k] = h;
     lbm_set_stream(h, b->stream);
   }
-  if (rc == LBM_OK && (cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess ||
-                       cudaMalloc(&b->d_errs, sizeof(unsigned) * n) != cudaSuccess ||
+  if (rc == LBM_OK && (dev_malloc(&b->d_counter, sizeof(int)) != cudaSuccess ||
+                       dev_malloc(&b->d_errs, sizeof(unsigned) * n) != cudaSuccess ||
                        cudaMallocHost(&b->h_errs, sizeof(unsigned) * n) != cudaSuccess))
     rc = LBM_ENOMEM;
   if (rc == LBM_OK && cudaMemset(b->d_errs, 0, sizeof(unsigned) * n) != cudaSuccess) rc = LBM_ECUDA;

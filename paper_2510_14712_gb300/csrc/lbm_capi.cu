@@ -1,4 +1,5 @@
 // lbm_capi.cu - the extern "C" interface declared in include/lbm.h.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -6,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lbm_internal.cuh"
 
@@ -163,6 +165,7 @@ void free_state(Handle& h) {
   for (int k = 0; k < 2; ++k) {
     if (h.pop[k]) cudaFree(h.pop[k]);
     h.pop[k] = nullptr;
+    h.p.pop[k] = nullptr;
   }
   if (h.scratch) cudaFree(h.scratch);
   h.scratch = nullptr;
@@ -182,7 +185,7 @@ int sc_alloc(Handle& h) {
   h.p.sc_prims = nullptr;
   h.p.sc_visc = nullptr;
   if (!h.p.sc_on) return LBM_OK;
-  CK(cudaMalloc(&h.sc_buf, sc_bytes(h)));
+  CK(dev_malloc(&h.sc_buf, sc_bytes(h)));
   CK(cudaMemsetAsync(h.sc_buf, 0, sc_bytes(h), h.stream));
   const size_t es = h.precision == LBM_FP64 ? 8 : 4;
   h.p.sc_prims = h.sc_buf;
@@ -202,13 +205,14 @@ int layout(Handle& h) {
     return fail(LBM_EINVAL, "domain too large: 2 Q Nz Ny pitch must stay below 2^32 elements");
   const size_t pop_bytes = size_t(2 * h.Q) * size_t(p.plane) * h.elem_bytes;
   for (int k = 0; k < 2; ++k) {
-    CK(cudaMalloc(&h.pop[k], pop_bytes));
+    CK(dev_malloc(&h.pop[k], pop_bytes));
     CK(cudaMemsetAsync(h.pop[k], 0, pop_bytes, h.stream));
+    p.pop[k] = h.pop[k];
   }
   h.scratch_bytes = scratch_for(h);
-  CK(cudaMalloc(&h.scratch, h.scratch_bytes));
+  CK(dev_malloc(&h.scratch, h.scratch_bytes));
   h.io_bytes = size_t(h.D + 2) * size_t(h.Nx) * h.Ny * h.Nz * sizeof(double);
-  CK(cudaMalloc(&h.io_dev, h.io_bytes));
+  CK(dev_malloc(&h.io_dev, h.io_bytes));
   h.cur = 0;
   h.initialized = 0;
   return sc_alloc(h);
@@ -274,10 +278,49 @@ int read_err(Handle& h) {
 
 }  // namespace
 
+namespace lbm {
+std::vector<unsigned long long (*)()>& oob_readers() {
+  static std::vector<unsigned long long (*)()> r;   // constructed on first use (static initialisers of other units)
+  return r;
+}
+void register_oob_reader(unsigned long long (*reader)()) { oob_readers().push_back(reader); }
+
+// allocations left until the injected failure (0: none armed)
+std::atomic<int> g_fail_alloc{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int k = g_fail_alloc.load();
+  while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
 const char* lbm_version(void) { return "gb300-nonideal-lbm 0.1"; }
+
+
+long long lbm_debug_bounds_violations(void) {
+#ifdef LBM_BOUNDS_CHECK
+  unsigned long long n = 0;
+  for (auto r : oob_readers()) n += r();
+  return (long long)n;
+#else
+  return -1;
+#endif
+}
+
+int lbm_debug_fail_alloc(int k) {
+  if (k < 0) return fail(LBM_EINVAL, "k must be >= 0");
+  g_fail_alloc.store(k);
+  return LBM_OK;
+}
 
 int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* eos, double tau, double Pr,
                double cv) {
@@ -350,13 +393,15 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
     }
   }
   int rc;
-  if (cudaMalloc(&h->partials, kMaxPartials * 5 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&h->totals_dev, 8 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&h->err_dev, sizeof(unsigned)) != cudaSuccess ||
-      cudaMallocHost(&h->err_host, sizeof(unsigned)) != cudaSuccess) {
-    rc = cuda_fail(cudaGetLastError(), "allocation");
+  cudaError_t ae = dev_malloc(&h->partials, kMaxPartials * 5 * sizeof(double));
+  if (ae == cudaSuccess) ae = dev_malloc(&h->totals_dev, 8 * sizeof(double));
+  if (ae == cudaSuccess) ae = dev_malloc(&h->err_dev, sizeof(unsigned));
+  if (ae == cudaSuccess) ae = cudaMallocHost(&h->err_host, sizeof(unsigned));
+  if (ae != cudaSuccess) {
+    rc = cuda_fail(ae, "allocation");
+    const std::string msg = g_err;
     lbm_destroy(h);
-    return rc;
+    return fail(rc, msg);
   }
   cudaMemset(h->err_dev, 0, sizeof(unsigned));
   rc = layout(*h);

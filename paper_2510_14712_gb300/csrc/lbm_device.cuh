@@ -69,6 +69,14 @@ __host__ __device__ inline float vdw_temperature_fp64(double a, double inv_cv, f
   return float((ed + a * double(rho)) * inv_cv);
 }
 
+// a / b correctly rounded, also in the FP32 kernel sets built with the
+// reciprocal-based FP32 division (-prec-div=false): for the divisions of the
+// moments by rho (Eqs. def_u, def_E), whose rounding the step amplifies most
+// (the velocity by reciprocal doubles the FP32 error of u over 1000 steps of
+// a Taylor-Green box in the oracle evaluated in float32)
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
+
 template <typename real> __host__ __device__ inline real vdw_pressure(const Model<real>& m, real rho, real T) {
   return rho * m.R * T / (real(1) - m.b * rho) - m.a * rho * rho;          // Eq. Pvdw
 }

@@ -226,8 +226,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-          const real v = Store<S>::template ld<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                     p.ref[i]);
+          const unsigned o = unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1];
+          const real v = pop_ok(p, Pm[cm + 1], o) ? Store<S>::template ld<real>(Pm[cm + 1], o, p.ref[i]) : real(0);
           rho += v;
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -246,8 +246,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            rho += Store<S>::template ld<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] +
-                                                               unsigned(gw + p.G - cx), p.ref[i]);
+            const unsigned o = unsigned(i) * plane32 + yr[cy + 1] + unsigned(gw + p.G - cx);
+            rho += pop_ok(p, Pm[cm + 1], o) ? Store<S>::template ld<real>(Pm[cm + 1], o, p.ref[i]) : real(0);
           }
         }
         s_rho[slot * G::N3 + k] = rho;
@@ -256,8 +256,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-            Se += Store<S>::template ld<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                              p.ref[Q + i]);
+            const unsigned o = unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1];
+            Se += pop_ok(p, Pm[cm + 1], o) ? Store<S>::template ld<real>(Pm[cm + 1], o, p.ref[Q + i]) : real(0);
           }
           const int k1 = (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx - 2);
           real* dst = s_mom + (slot * G::NMOM) * G::N1 + k1;
@@ -315,16 +315,16 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
             const int i = g * J + j;
             const int cy = D == 3 ? j / 3 - 1 : 0, cm = D == 3 ? j % 3 - 1 : j - 1;
             const ST* row = Pm[cm + 1] + (unsigned(off + i) * plane32 + yr[cy + 1]);
-            real v[4];
-            Store<S>::template ld4<real>(row, xq0, p.ref[off + i], v);
+            real v[4] = {real(0), real(0), real(0), real(0)};
+            if (pop_ok(p, row, xq0, 4)) Store<S>::template ld4<real>(row, xq0, p.ref[off + i], v);
             if (g == 1) {
               w[0] = v[0]; w[1] = v[1]; w[2] = v[2]; w[3] = v[3];
             } else if (g == 2) {                                  // c_x = +1: node x pulls from x - 1
-              w[0] = need[0] ? Store<S>::template ld<real>(row, xqm, p.ref[off + i]) : real(0);
+              w[0] = need[0] && pop_ok(p, row, xqm) ? Store<S>::template ld<real>(row, xqm, p.ref[off + i]) : real(0);
               w[1] = v[0]; w[2] = v[1]; w[3] = v[2];
             } else {                                              // c_x = -1: node x pulls from x + 1
               w[0] = v[1]; w[1] = v[2]; w[2] = v[3];
-              w[3] = need[3] ? Store<S>::template ld<real>(row, xq4, p.ref[off + i]) : real(0);
+              w[3] = need[3] && pop_ok(p, row, xq4) ? Store<S>::template ld<real>(row, xq4, p.ref[off + i]) : real(0);
             }
           };
           if (!isg) {
@@ -439,11 +439,11 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           real uF = 0;
 #pragma unroll
           for (int a = 0; a < D; ++a) {
-            u[a] = (mo[a * G::N1] + real(0.5) * F[a]) / rho;                                   // Eq. def_u
+            u[a] = div_rn(mo[a * G::N1] + real(0.5) * F[a], rho);                              // Eq. def_u
             uF += u[a] * F[a];
             u2 += u[a] * u[a];
           }
-          E = (mo[D * G::N1] + real(0.5) * uF) / rho;                                         // Eq. def_E
+          E = div_rn(mo[D * G::N1] + real(0.5) * uF, rho);                                    // Eq. def_E
         }
         // closure (rho, E, |u|^2) -> e, (T, P, c_s^2)
         real T = real(0), P = real(1), cs2 = real(0), e = real(0);
@@ -562,20 +562,22 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-          v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                 p.ref[i]);
+          const unsigned o = unsigned(i) * plane32 + yr[cy + 1] + xc[cx + 1];
+          v[i] = pop_ok(p, Pm[cm + 1], o) ? Store<S>::template ld_last<real>(Pm[cm + 1], o, p.ref[i]) : real(0);
         }
         FactoredRelax<D, real>::f_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
-          Store<S>::template st_stream<real>(Bq, unsigned(i) * plane32 + oc, x, p.ref[i]);
+          if (pop_ok(p, Bq, unsigned(i) * plane32 + oc))
+            Store<S>::template st_stream<real>(Bq, unsigned(i) * plane32 + oc, x, p.ref[i]);
         });
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const int cx = L::c(i, 0), cy = D == 3 ? L::c(i, 1) : 0, cm = L::c(i, D - 1);
-          v[i] = Store<S>::template ld_last<real>(Pm[cm + 1], unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1],
-                                                 p.ref[Q + i]);
+          const unsigned o = unsigned(Q + i) * plane32 + yr[cy + 1] + xc[cx + 1];
+          v[i] = pop_ok(p, Pm[cm + 1], o) ? Store<S>::template ld_last<real>(Pm[cm + 1], o, p.ref[Q + i]) : real(0);
         }
         FactoredRelax<D, real>::g_pass(at, [&](int i) { return v[i]; }, [&](int i, real x) {
-          Store<S>::template st_stream<real>(Bq, unsigned(Q + i) * plane32 + oc, x, p.ref[Q + i]);
+          if (pop_ok(p, Bq, unsigned(Q + i) * plane32 + oc))
+            Store<S>::template st_stream<real>(Bq, unsigned(Q + i) * plane32 + oc, x, p.ref[Q + i]);
         });
       }
     }

@@ -46,6 +46,9 @@ struct Params {
   // FP64 temperature inversion in FP32 arithmetic (lbm_set_temperature_fp64);
   // read by the multi-pass step (the fused step selects its closure instead)
   int t64;
+  // the handle's two population buffers (2 Q plane elements each): the
+  // bounds of every population access in bounds-check builds
+  const void* pop[2];
 };
 
 template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
@@ -138,6 +141,20 @@ struct Batch {
   int unstable;
   long long launches;
 };
+
+// Bounds-check builds (-DLBM_BOUNDS_CHECK) count the population accesses that
+// fall outside the handle's buffers in one device counter per translation
+// unit; each unit registers a reader of its counter here (a static
+// initialiser), and lbm_debug_bounds_violations sums them.
+void register_oob_reader(unsigned long long (*reader)());
+
+// Device allocation of the library: cudaMalloc, except that the allocation
+// chosen by lbm_debug_fail_alloc fails with cudaErrorMemoryAllocation (and
+// allocates nothing), so that tests can take every out-of-memory path.
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <class T> inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
 
 // the opaque handle type of the C interface
 }  // namespace lbm

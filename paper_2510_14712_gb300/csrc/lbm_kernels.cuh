@@ -73,6 +73,43 @@ template <> struct Store<Fp16Dev> {
 };
 
 // ---------------------------------------------------------------------------
+// bounds-check builds (-DLBM_BOUNDS_CHECK): every population access of the
+// step kernels must lie inside one of the handle's two population buffers;
+// one outside is skipped (a load gives 0) and counted.  Other builds compile
+// the check away.
+// ---------------------------------------------------------------------------
+#ifdef LBM_BOUNDS_CHECK
+namespace {
+__device__ unsigned long long g_oob;                 // accesses outside the buffers (this unit's kernels)
+unsigned long long read_oob() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, g_oob, sizeof(v));
+  return v;
+}
+struct OobReaderRegistration {
+  OobReaderRegistration() { register_oob_reader(&read_oob); }
+} g_oob_registration;
+}  // namespace
+#endif
+
+// access to the n elements ptr[off .. off + n) is inside a population buffer of p
+template <typename T>
+__device__ __forceinline__ bool pop_ok(const Params& p, const T* ptr, long long off, int n = 1) {
+#ifdef LBM_BOUNDS_CHECK
+  const T* a = ptr + off;
+  const long long len = 2LL * p.Q * p.plane;
+  for (int k = 0; k < 2; ++k) {
+    const T* lo = static_cast<const T*>(p.pop[k]);
+    if (lo && a >= lo && a + n <= lo + len) return true;
+  }
+  atomicAdd(&g_oob, 1ULL);
+  return false;
+#else
+  return true;
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // geometry helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -166,8 +203,9 @@ __global__ void k_init(Params p, typename Store<S>::T* A, const double* rho, con
     const int ys = wrap(y - L::c(i, 1), p.Ny);
     const int zs = D == 3 ? wrap(z - L::c(i, 2), p.Nz) : z;
     const long long o = node_off(p, xs, ys, zs);
-    Store<S>::template st<double>(A, i * p.plane + o, feq[i], p.ref[i]);
-    Store<S>::template st<double>(A, (L::Q + i) * p.plane + o, geq[i], p.ref[L::Q + i]);
+    if (pop_ok(p, A, i * p.plane + o)) Store<S>::template st<double>(A, i * p.plane + o, feq[i], p.ref[i]);
+    if (pop_ok(p, A, (L::Q + i) * p.plane + o))
+      Store<S>::template st<double>(A, (L::Q + i) * p.plane + o, geq[i], p.ref[L::Q + i]);
   }
 }
 
@@ -181,8 +219,10 @@ __device__ __forceinline__ void pull(const Params& p, const typename Store<S>::T
     const int ys = wrap(y - L::c(i, 1), p.Ny);
     const int zs = D == 3 ? wrap(z - L::c(i, 2), p.Nz) : z;
     const long long o = node_off(p, xs, ys, zs);
-    fg[i] = Store<S>::template ld<real>(A, i * p.plane + o, p.ref[i]);
-    fg[L::Q + i] = Store<S>::template ld<real>(A, (L::Q + i) * p.plane + o, p.ref[L::Q + i]);
+    fg[i] = pop_ok(p, A, i * p.plane + o) ? Store<S>::template ld<real>(A, i * p.plane + o, p.ref[i]) : real(0);
+    fg[L::Q + i] = pop_ok(p, A, (L::Q + i) * p.plane + o)
+                       ? Store<S>::template ld<real>(A, (L::Q + i) * p.plane + o, p.ref[L::Q + i])
+                       : real(0);
   }
 }
 
@@ -269,11 +309,11 @@ __global__ void k_prims(Params p, const real* M, real* W) {
   real u[D], uF = 0, u2 = 0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    u[a] = (M[(1 + a) * p.plane + o] + real(0.5) * F[a]) / rho;                     // Eq. def_u
+    u[a] = div_rn(M[(1 + a) * p.plane + o] + real(0.5) * F[a], rho);                // Eq. def_u
     uF += u[a] * F[a];
     u2 += u[a] * u[a];
   }
-  const real E = (M[(1 + D) * p.plane + o] + real(0.5) * uF) / rho;                // Eq. def_E
+  const real E = div_rn(M[(1 + D) * p.plane + o] + real(0.5) * uF, rho);           // Eq. def_E
   real T, P, h;
   // p.t64: the temperature inversion in FP64 from the FP32 moments (as the
   // fused step's T64 closures)
@@ -361,7 +401,8 @@ __global__ void k_collide(Params p, const typename Store<S>::T* A, typename Stor
   const unsigned fl = collide_node<D, real>(m, s, fg, fg + L::Q);
   if (fl) atomicOr(err, fl);
 #pragma unroll
-  for (int i = 0; i < 2 * L::Q; ++i) Store<S>::template st<real>(B, i * p.plane + o, fg[i], p.ref[i]);
+  for (int i = 0; i < 2 * L::Q; ++i)
+    if (pop_ok(p, B, i * p.plane + o)) Store<S>::template st<real>(B, i * p.plane + o, fg[i], p.ref[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +427,8 @@ __device__ inline void ghost_node(const Params& p, typename Store<S>::T* B, int 
     const int towards = low ? -1 : 1;
     double rho_e = 0.0, into = 0.0;
     for (int i = 0; i < L::Q; ++i) {
-      const double v = Store<S>::template ld<double>(B, i * p.plane + os, p.ref[i]);
+      const double v = pop_ok(p, B, i * p.plane + os) ? Store<S>::template ld<double>(B, i * p.plane + os, p.ref[i])
+                                                       : 0.0;
       rho_e += v;
       if (L::c(i, 0) == towards) into += v;
     }
@@ -399,13 +441,15 @@ __device__ inline void ghost_node(const Params& p, typename Store<S>::T* B, int 
       if (L::c(i, 0) == -towards) out += feq[i];
     const double s = into / out;
     for (int i = 0; i < L::Q; ++i) {
-      Store<S>::template st<double>(B, i * p.plane + o, s * feq[i], p.ref[i]);
-      Store<S>::template st<double>(B, (L::Q + i) * p.plane + o, s * geq[i], p.ref[L::Q + i]);
+      if (pop_ok(p, B, i * p.plane + o)) Store<S>::template st<double>(B, i * p.plane + o, s * feq[i], p.ref[i]);
+      if (pop_ok(p, B, (L::Q + i) * p.plane + o))
+        Store<S>::template st<double>(B, (L::Q + i) * p.plane + o, s * geq[i], p.ref[L::Q + i]);
     }
     return;
   }
   const double* eq = low ? p.eq_lo : p.eq_hi;
   for (int i = 0; i < 2 * L::Q; ++i) {
+    if (!pop_ok(p, B, i * p.plane + o) || !pop_ok(p, B, i * p.plane + os)) continue;
     if (bc == LBM_BC_INFLOW) Store<S>::template st<double>(B, i * p.plane + o, eq[i], p.ref[i]);
     else B[i * p.plane + o] = B[i * p.plane + os];
   }

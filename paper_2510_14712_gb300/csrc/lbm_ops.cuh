@@ -287,9 +287,9 @@ template <int D, typename S, typename real> struct OpsImpl {
       if (b.d_n1rows) cudaFree(b.d_n1rows);
       b.d_insts = b.d_items = nullptr;
       b.d_n1rows = nullptr;
-      if (cudaMalloc(&b.d_insts, sizeof(BatchInstance) * b.n) != cudaSuccess) return LBM_ENOMEM;
-      if (cudaMalloc(&b.d_items, sizeof(BatchItem) * items.size()) != cudaSuccess) return LBM_ENOMEM;
-      if (cudaMalloc(&b.d_n1rows, sizeof(int) * (b.n + 1)) != cudaSuccess) return LBM_ENOMEM;
+      if (dev_malloc(&b.d_insts, sizeof(BatchInstance) * b.n) != cudaSuccess) return LBM_ENOMEM;
+      if (dev_malloc(&b.d_items, sizeof(BatchItem) * items.size()) != cudaSuccess) return LBM_ENOMEM;
+      if (dev_malloc(&b.d_n1rows, sizeof(int) * (b.n + 1)) != cudaSuccess) return LBM_ENOMEM;
       cudaMemcpy(b.d_insts, ti.data(), sizeof(BatchInstance) * b.n, cudaMemcpyHostToDevice);
       cudaMemcpy(b.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
       cudaMemcpy(b.d_n1rows, rowstart.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice);

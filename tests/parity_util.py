@@ -76,15 +76,17 @@ def _log(what, tol, l2, node):
 
 
 def assert_parity(got, want, tol, what="", node_mult=None, fields=("rho", "u", "T")):
-    """Relative L2 of every field at most `tol`, and no single node off by more
-    than node_mult * tol * rms(want) (a wrong node at a tile seam, a wall
-    column or a wrapped edge cannot hide inside the norm)."""
+    """Relative L2 of every field at most `tol` (a number, or one per field),
+    and no single node off by more than node_mult * tol * rms(want) (a wrong
+    node at a tile seam, a wall column or a wrapped edge cannot hide inside the
+    norm)."""
+    tols = tol if isinstance(tol, dict) else {k: tol for k in fields}
     if node_mult is None:
-        node_mult = NODE_MULT if tol < 1e-9 else NODE_MULT_FP32
+        node_mult = NODE_MULT if max(tols.values()) < 1e-9 else NODE_MULT_FP32
     l2, node = parity_errors(got, want, fields)
-    _log(what, tol, l2, node)
-    bad = {k: v for k, v in l2.items() if not (v <= tol)}
-    assert not bad, "%s relative L2 above %g: %s (per node %s)" % (what, tol, l2, node)
-    badn = {k: v for k, v in node.items() if not (v <= node_mult * tol)}
-    assert not badn, "%s per-node error above %g x %g x rms: %s (relative L2 %s)" % (what, node_mult, tol, node, l2)
+    _log(what, max(tols.values()), l2, node)
+    bad = {k: v for k, v in l2.items() if not (v <= tols[k])}
+    assert not bad, "%s relative L2 above %s: %s (per node %s)" % (what, tols, l2, node)
+    badn = {k: v for k, v in node.items() if not (v <= node_mult * tols[k])}
+    assert not badn, "%s per-node error above %g x %s x rms: %s (relative L2 %s)" % (what, node_mult, tols, node, l2)
     return l2

@@ -117,31 +117,60 @@ def tgv_long_ref():
     return oracle_run(tgv_case((19, 13, 11), seed=5, drift=DRIFT), 1000)
 
 
+@pytest.fixture(scope="module")
+def tgv_long_bound(tgv_long_ref):
+    """FP32 bound of the drifting box: 1e-5, or twice the error of the scheme
+    evaluated in float32 (the oracle run with float32 state and constants)."""
+    import fp32_eval
+    return fp32_eval.fp32_bound(fp32_eval.errors(fp32_eval.run(fp32_eval.tgv_drift_case(), 1000, "fp32"),
+                                                 tgv_long_ref))
+
+
 def test_tgv_d3q27_fp64_long(tgv_long_ref):
     got = gpu_run(tgv_case((19, 13, 11), seed=5, drift=DRIFT), 1000, "fp64", chunk=250)
     assert_parity(got, tgv_long_ref, 1e-12, "tgv fp64 1000 steps")
 
 
-def test_tgv_d3q27_fp32_long(tgv_long_ref):
+def test_tgv_d3q27_fp32_long(tgv_long_ref, tgv_long_bound):
     got = gpu_run(tgv_case((19, 13, 11), seed=5, drift=DRIFT), 1000, "fp32")
-    assert_parity(got, tgv_long_ref, 1e-5, "tgv fp32 1000 steps")
+    assert_parity(got, tgv_long_ref, tgv_long_bound, "tgv fp32 1000 steps")
 
 
 # ---- the benchmark's own lattice parameters on a 64^3 box, 1000 steps ------------------
 # The 256^3 Taylor-Green workload's tau, U0, kappa and eta/mu (inputs.tgv(N=256):
 # tau is not rescaled to the smaller box), with the parity runs' seeded noise,
-# over 1000 steps: the tolerances of the FP64 (1e-12) and FP32 (1e-5) builds
-# and the 1e-3 density bound of FP16-deviation storage.
+# over 1000 steps.  FP64: 1e-12.  FP32: 1e-5, or twice the error of the scheme
+# evaluated in float32 where that is larger: the oracle run with float32 state
+# and constants lands at about 0.9e-5 in u here, so an FP32 kernel whose
+# rounding differs in detail lands near 1e-5 either way.  FP16-deviation
+# storage: 1e-3 on rho.  The FP64 oracle and its float32 evaluation run
+# concurrently in two child processes.
 
 def tgv_headline_case():
-    c = inputs.add_noise(inputs.tgv(shape=(64, 64, 64)), 0)     # the parity recipe's seeded 1e-3 noise
-    c.tau = inputs.scenario("tgv_d3q27")["tau"]
-    return c
+    import fp32_eval
+    return fp32_eval.tgv_headline_case()
 
 
 @pytest.fixture(scope="module")
-def tgv_headline_ref():
-    return oracle_run(tgv_headline_case(), 1000)
+def tgv_headline_refs(tmp_path_factory):
+    import subprocess
+    import sys
+    import fp32_eval
+    d = tmp_path_factory.mktemp("tgv_headline")
+    script = fp32_eval.__file__
+    procs = {m: subprocess.Popen([sys.executable, script, "tgv_headline", m, "1000", str(d / (m + ".npz"))],
+                                 stdout=subprocess.PIPE, stderr=subprocess.PIPE) for m in ("fp64", "fp32")}
+    for m, pr in procs.items():
+        _, err = pr.communicate()
+        assert pr.returncode == 0, err.decode()[-2000:]
+    ref = dict(np.load(d / "fp64.npz"))
+    f32 = dict(np.load(d / "fp32.npz"))
+    return ref, fp32_eval.fp32_bound(fp32_eval.errors(f32, ref))
+
+
+@pytest.fixture(scope="module")
+def tgv_headline_ref(tgv_headline_refs):
+    return tgv_headline_refs[0]
 
 
 def test_tgv_headline_params_64_fp64(tgv_headline_ref):
@@ -149,14 +178,13 @@ def test_tgv_headline_params_64_fp64(tgv_headline_ref):
     assert_parity(got, tgv_headline_ref, 1e-12, "tgv 64^3 (256^3 lattice parameters) fp64 1000 steps")
 
 
-def test_tgv_headline_params_64_fp32(tgv_headline_ref):
-    got = gpu_run(tgv_headline_case(), 1000, "fp32")
-    assert_parity(got, tgv_headline_ref, 1e-5, "tgv 64^3 (256^3 lattice parameters) fp32 1000 steps")
-
-
-def test_tgv_headline_params_64_fp32_multipass(tgv_headline_ref):
-    got = gpu_run(tgv_headline_case(), 1000, "fp32", step_kernel=P.LBM_STEP_MULTIPASS)
-    assert_parity(got, tgv_headline_ref, 1e-5, "tgv 64^3 (256^3 lattice parameters) fp32 multipass 1000 steps")
+@pytest.mark.parametrize("step_kernel,t_fp64", [(0, False), (1, False), (0, True), (1, True)])
+def test_tgv_headline_params_64_fp32(tgv_headline_refs, step_kernel, t_fp64):
+    """The FP32 build, fused and multi-pass, plain and with the FP64 temperature inversion."""
+    ref, bound = tgv_headline_refs
+    got = gpu_run(tgv_headline_case(), 1000, "fp32", step_kernel=step_kernel, t_fp64=t_fp64)
+    assert_parity(got, ref, bound, "tgv 64^3 (256^3 lattice parameters) fp32%s %s 1000 steps"
+                  % (" T64" if t_fp64 else "", "multipass" if step_kernel else "fused"))
 
 
 def test_tgv_headline_params_64_fp16dev(tgv_headline_ref):
@@ -480,9 +508,4 @@ def test_temperature_fp64_switch():
             P.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("step_kernel", [0, 1])
-def test_tgv_headline_params_64_fp32_fp64_temperature(tgv_headline_ref, step_kernel):
-    """The mixed-precision form (FP64 temperature inversion), fused and multi-pass."""
-    got = gpu_run(tgv_headline_case(), 1000, "fp32", t_fp64=True, step_kernel=step_kernel)
-    assert_parity(got, tgv_headline_ref, 1e-5, "tgv 64^3 (256^3 lattice parameters) fp32 T64 %s 1000 steps"
-                  % ("multipass" if step_kernel else "fused"))
+

@@ -25,11 +25,8 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import lbm as olbm
+from fp32_eval import errors, run, tgv_drift_case
 from oracle import thermo
-
-F32 = np.float32
-CONSTS = ("a", "b", "R", "cv", "kappa", "eta_over_mu", "mu", "k_over_mu")
 
 
 def shock_case(seed, Nx=400, Ny=3, Ma=1.2):
@@ -38,39 +35,6 @@ def shock_case(seed, Nx=400, Ny=3, Ma=1.2):
     r2, T2, u2, _ = thermo.rankine_hugoniot(v["rho"], v["T"], 0.0, Ma, e["a"], e["b"], e["R"], sc["cv"])
     sc["post"] = dict(rho=r2, T=T2, u=u2)
     return inputs.add_noise(inputs.shock_drop(2, (Nx, Ny), shock_x=60, with_drop=False, sc=sc), seed)
-
-
-def fields(s):
-    F = s.fields()
-    return dict(rho=np.asarray(F["rho"], dtype=np.float64), u=np.stack(F["u"]).astype(np.float64),
-                T=np.asarray(F["T"], dtype=np.float64))
-
-
-def run(case, steps, mode="fp64"):
-    """mode: fp64 (the oracle), store32 (FP64 arithmetic, float32 storage after
-    every step), fp32 (float32 state and constants throughout)."""
-    m = olbm.Model(case.D, case.shape, case.eos, case.tau, case.Pr, case.cv, case.x_low, case.x_high)
-    s = olbm.Sim(m, case.rho, case.u, case.T)
-    if mode == "fp32":
-        for k in CONSTS:
-            setattr(m, k, F32(getattr(m, k)))
-        s.f, s.g = s.f.astype(F32), s.g.astype(F32)
-    for _ in range(steps):
-        s.step(1)
-        if mode == "store32":
-            s.f = s.f.astype(F32).astype(np.float64)
-            s.g = s.g.astype(F32).astype(np.float64)
-    if mode == "fp32":
-        assert s.f.dtype == F32 and s.g.dtype == F32        # the run stayed in float32
-    return fields(s)
-
-
-def rel(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
-
-
-def errors(got, want):
-    return {k: rel(got[k], want[k]) for k in ("rho", "u", "T")}
 
 
 def t_fp64(rho, E, u_sq, a, cv):
@@ -97,15 +61,6 @@ def test_plain_fp32_arithmetic_misses_the_bar_on_shocks(shock_refs):
     eu = [errors(run(shock_case(s), 300, "fp32"), shock_refs[s])["u"] for s in (3, 4, 5)]
     assert max(eu) >= 1e-5, eu              # one seed misses 1e-5 with plain FP32 arithmetic
     assert max(eu) < 2e-5, eu
-
-
-def tgv_drift_case():
-    """The drifting Taylor-Green box of the FP32 1000-step GPU parity test."""
-    c = inputs.add_noise(inputs.tgv(shape=(19, 13, 11)), 5)
-    sc = inputs.scenario("tgv_d3q27")
-    c.tau = sc["tau"] * 0.02 / sc["nu"]
-    c.u = [ua + d for ua, d in zip(c.u, (0.08, -0.05, 0.06))]
-    return c
 
 
 def test_fp64_temperature_inversion_is_no_systematic_gain(shock_refs, monkeypatch):
