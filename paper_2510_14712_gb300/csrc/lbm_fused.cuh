@@ -185,11 +185,6 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   using ST = typename Store<S>::T;
   // element offsets inside a population buffer fit 32 bits (checked at create)
   const unsigned plane32 = unsigned(p.plane), pitch32 = unsigned(p.pitch);
-  // stage A by quads of four x nodes (vector loads): x rows of 4-aligned
-  // quads, i.e. a periodic x of a multiple of 4 nodes (quads wrap whole) at
-  // least a tile plus two quads wide, or ghost-padded x (quad starts at padded
-  // multiples of 4; pitch >= Nx + 8 keeps every needed quad in its row)
-  const bool vec = !SMALL && TX % 4 == 0 && (!p.periodic_x || (p.Nx % 4 == 0 && p.Nx >= TX + 8));
 
   for (int pl = mb - 3; pl <= me + 2; ++pl) {
     // ---------------- A: moments of plane pl --------------------------------
@@ -266,127 +261,10 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
           dst[D * G::N1] = Se;
         }
       };
-      if (vec && !wtile) {
-        // Quads of four x nodes: tasks are (row, quad) of the R3 box for f
-        // (rho, and j on R1) and of the R1 box for g (S).  Per direction one
-        // vector load covers the quad's sources for c_x = 0; the sources of
-        // c_x = +1 (x - 1) and -1 (x + 1) are shifted by one node, and the one
-        // outside the quad is a scalar load, made only when that node is
-        // needed.  Each node sums its populations in the direction order of
-        // the scalar path, so both give bitwise the same moments.
-        constexpr int NQ = TX / 4 + 2;                            // quads per row: x0 - 4 .. x0 + TX + 3
-        constexpr int NF = NQ * G::BY3, NTASK = NQ * (G::BY3 + G::BY1);
+      constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
 #pragma unroll 1
-        for (int t = tid; t < NTASK; t += G::NT) {
-          const bool isg = t >= NF;
-          const int tt = isg ? t - NF : t;
-          const int qx = tt % NQ;
-          const int ly = isg ? tt / NQ + (G::HY3 - G::HY1) : tt / NQ;   // row of the R3 box
-          const int oy = D == 3 ? outside(ly, G::HY3, hy) : 0;
-          const int lim = isg ? 1 : 3;
-          if (oy > lim) continue;
-          const int xq = x0 - 4 + 4 * qx;                         // interior x of the quad's first node
-          bool need[4], in1[4];
-          bool any = false;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int ox = outside(xq + k - x0 + 3, 3, TX);
-            need[k] = ox + oy <= lim && xq + k >= xmin && xq + k <= xmax;
-            in1[k] = need[k] && ox + oy <= 1;
-            any = any || need[k];
-          }
-          if (!any) continue;
-          const int gy = D == 3 ? wrapc<false>(y0 + ly - G::HY3, p.Ny) : 0;
-          unsigned yr[3];
-#pragma unroll
-          for (int c = -1; c <= 1; ++c) yr[c + 1] = D == 3 ? unsigned(wrapc<false>(gy - c, p.Ny)) * pitch32 : 0u;
-          const unsigned xq0 = unsigned(p.periodic_x ? wrapc<false>(xq, p.Nx) : xq + p.G);
-          const unsigned xqm = unsigned(p.periodic_x ? wrapc<false>(xq - 1, p.Nx) : xq + p.G - 1);
-          const unsigned xq4 = unsigned(p.periodic_x ? wrapc<false>(xq + 4, p.Nx) : xq + p.G + 4);
-          const int lx0 = xq - x0 + 3;                            // R3-box x of the quad's first node
-          // The directions in three groups of c_x = g - 1 (i = g Q/3 + j), a rolled
-          // loop so that one group's loads are in flight at a time (all 27
-          // vector loads at once would not fit the register budget); within a
-          // group j fixes the other components.  Every accumulation chain still
-          // runs in increasing i.
-          // pulled values of the quad's four nodes for direction i = g Q/3 + j of kind f (off 0) or g (off Q)
-          auto pulled = [&](const int g, const int j, const int off, real* w) {
-            constexpr int J = Q / 3;
-            const int i = g * J + j;
-            const int cy = D == 3 ? j / 3 - 1 : 0, cm = D == 3 ? j % 3 - 1 : j - 1;
-            const ST* row = Pm[cm + 1] + (unsigned(off + i) * plane32 + yr[cy + 1]);
-            real v[4] = {real(0), real(0), real(0), real(0)};
-            if (pop_ok(p, row, xq0, 4)) Store<S>::template ld4<real>(row, xq0, p.ref[off + i], v);
-            if (g == 1) {
-              w[0] = v[0]; w[1] = v[1]; w[2] = v[2]; w[3] = v[3];
-            } else if (g == 2) {                                  // c_x = +1: node x pulls from x - 1
-              w[0] = need[0] && pop_ok(p, row, xqm) ? Store<S>::template ld<real>(row, xqm, p.ref[off + i]) : real(0);
-              w[1] = v[0]; w[2] = v[1]; w[3] = v[2];
-            } else {                                              // c_x = -1: node x pulls from x + 1
-              w[0] = v[1]; w[1] = v[2]; w[2] = v[3];
-              w[3] = need[3] && pop_ok(p, row, xq4) ? Store<S>::template ld<real>(row, xq4, p.ref[off + i]) : real(0);
-            }
-          };
-          if (!isg) {
-            real rho[4], sp[4][D], sn[4][D];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              rho[k] = real(0);
-#pragma unroll
-              for (int a = 0; a < D; ++a) sp[k][a] = sn[k][a] = real(0);
-            }
-#pragma unroll 1
-            for (int g = 0; g < 3; ++g) {
-#pragma unroll
-              for (int j = 0; j < Q / 3; ++j) {
-                real w[4];
-                pulled(g, j, 0, w);
-                const int c1 = D == 3 ? j / 3 - 1 : j - 1, c2 = D == 3 ? j % 3 - 1 : 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                  rho[k] += w[k];
-                  if (g == 2) sp[k][0] += w[k];
-                  if (g == 0) sn[k][0] += w[k];
-                  if (c1 == 1) sp[k][1] += w[k];
-                  if (c1 == -1) sn[k][1] += w[k];
-                  if (D == 3 && c2 == 1) sp[k][D - 1] += w[k];
-                  if (D == 3 && c2 == -1) sn[k][D - 1] += w[k];
-                }
-              }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              if (need[k]) s_rho[slot * G::N3 + ly * G::BX3 + lx0 + k] = rho[k];
-              if (in1[k]) {
-                real* dst = s_mom + (slot * G::NMOM) * G::N1 + (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx0 + k - 2);
-#pragma unroll
-                for (int a = 0; a < D; ++a) dst[a * G::N1] = sp[k][a] - sn[k][a];
-              }
-            }
-          } else {
-            real Se[4] = {real(0), real(0), real(0), real(0)};
-#pragma unroll 1
-            for (int g = 0; g < 3; ++g) {
-#pragma unroll
-              for (int j = 0; j < Q / 3; ++j) {
-                real w[4];
-                pulled(g, j, Q, w);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) Se[k] += w[k];
-              }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (in1[k])
-                s_mom[(slot * G::NMOM + D) * G::N1 + (ly - (G::HY3 - G::HY1)) * G::BX1 + (lx0 + k - 2)] = Se[k];
-          }
-        }
-      } else {
-        constexpr int KFULL = G::N3 / G::NT, KREM = G::N3 % G::NT;
-#pragma unroll 1
-        for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
-        if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
-      }
+      for (int jp = 0; jp < KFULL; ++jp) moments(tid + jp * G::NT);
+      if (KREM > 0 && tid < KREM) moments(tid + KFULL * G::NT);
     }
     __syncthreads();
 

@@ -25,16 +25,9 @@ struct Fp16Dev {};  // tag: FP16 storage of p_i - p_i^ref
 template <typename S> struct Store;
 // ld/st: plain; ld_last: last read of the value in this step (evict-first);
 // st_stream: streaming store of the new populations (evict-first).
-// ld4: the four consecutive values p[o .. o+3] in one vector load (o a
-// multiple of 4, so the load is 32-, 16- or 8-byte aligned).
 template <> struct Store<double> {
   using T = double;
   template <typename real, typename I> __device__ static real ld(const T* p, I o, float) { return real(__ldg(p + o)); }
-  template <typename real, typename I> __device__ static void ld4(const T* p, I o, float, real* v) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p + o));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + o) + 1);
-    v[0] = real(a.x); v[1] = real(a.y); v[2] = real(b.x); v[3] = real(b.y);
-  }
   template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float) { return real(__ldcs(p + o)); }
   template <typename real, typename I> __device__ static void st(T* p, I o, real v, float) { p[o] = double(v); }
   template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float) { __stcs(p + o, double(v)); }
@@ -42,10 +35,6 @@ template <> struct Store<double> {
 template <> struct Store<float> {
   using T = float;
   template <typename real, typename I> __device__ static real ld(const T* p, I o, float) { return real(__ldg(p + o)); }
-  template <typename real, typename I> __device__ static void ld4(const T* p, I o, float, real* v) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(p + o));
-    v[0] = real(a.x); v[1] = real(a.y); v[2] = real(a.z); v[3] = real(a.w);
-  }
   template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float) { return real(__ldcs(p + o)); }
   template <typename real, typename I> __device__ static void st(T* p, I o, real v, float) { p[o] = float(v); }
   template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float) { __stcs(p + o, float(v)); }
@@ -54,12 +43,6 @@ template <> struct Store<Fp16Dev> {
   using T = __half;
   template <typename real, typename I> __device__ static real ld(const T* p, I o, float ref) {
     return real(__half2float(__ldg(p + o)) + ref);
-  }
-  template <typename real, typename I> __device__ static void ld4(const T* p, I o, float ref, real* v) {
-    const uint2 a = __ldg(reinterpret_cast<const uint2*>(p + o));
-    const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
-    const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
-    v[0] = real(lo.x + ref); v[1] = real(lo.y + ref); v[2] = real(hi.x + ref); v[3] = real(hi.y + ref);
   }
   template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float ref) {
     return real(__half2float(__ldcs(p + o)) + ref);

@@ -69,7 +69,20 @@ def tgv_drift_case():
     return c
 
 
-CASES = {"tgv_headline": tgv_headline_case, "tgv_drift": tgv_drift_case}
+def shock_case(seed=3, Nx=400, Ny=3, Ma=1.2):
+    """Ma 1.2 D2Q9 shock tube in the shock-drop scenario's vapour (post-state from
+    the oracle's Rankine-Hugoniot solver), shock at x = 60, seeded noise."""
+    import copy
+    from oracle import thermo
+    sc = copy.deepcopy(inputs.scenario("shock_drop_d2q9"))
+    e, v = sc["eos"], sc["vapour"]
+    r2, T2, u2, _ = thermo.rankine_hugoniot(v["rho"], v["T"], 0.0, Ma, e["a"], e["b"], e["R"], sc["cv"])
+    sc["post"] = dict(rho=r2, T=T2, u=u2)
+    return inputs.add_noise(inputs.shock_drop(2, (Nx, Ny), shock_x=60, with_drop=False, sc=sc), seed)
+
+
+CASES = {"tgv_headline": tgv_headline_case, "tgv_drift": tgv_drift_case, "riemann": lambda: inputs.riemann(),
+         "shock_tube": shock_case}
 
 
 def fp32_bound(e32, floor=1e-5, factor=2.0):

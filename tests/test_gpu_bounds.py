@@ -5,7 +5,7 @@ tests/bounds_cases.py -- the 8^3 and 16x4 boxes, stage A by quads of x nodes
 and its scalar fallback, ghost and wall fills, the multi-pass and batched
 steps -- run in a child process on that build: no access may fall outside,
 and the fields must agree with the regular build's to the rounding of each
-case's precision."""
+case's precision (the two builds contract multiply-adds differently)."""
 import os
 import subprocess
 import sys
@@ -44,8 +44,9 @@ def test_bounds_check_build_finds_no_out_of_buffer_access(tmp_path):
     want = bounds_cases.run_all(P)
     # the checks change no arithmetic, but the code around each access changes
     # shape, and with it the compiler's choice of fused multiply-adds: results
-    # agree to the rounding of the build's precision, not bit for bit
+    # agree to the rounding of the build's precision, not bit for bit (FP32:
+    # 1e-4 over 12 steps of boxes with 1% noise, where u is small)
     for k, v in want.items():
-        tol = 1e-12 if "fp64" in k else (1e-3 if "fp16" in k else 1e-5)
+        tol = 1e-12 if "fp64" in k else (1e-3 if "fp16" in k else 1e-4)
         err = np.linalg.norm((got[k] - v).ravel()) / max(np.linalg.norm(v.ravel()), 1e-300)
         assert err <= tol, (k, err)

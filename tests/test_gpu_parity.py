@@ -7,7 +7,6 @@ finishes in seconds, with ragged extents so that no dimension is a
 multiple of a tile; the full-size Taylor-Green workload is checked on
 sampled nodes against the oracle evaluated on a window around each sample.
 """
-import copy
 
 import numpy as np
 import pytest
@@ -48,22 +47,24 @@ def tgv_case(shape, nu=0.02, seed=0, drift=None):
 
 DRIFT = (0.08, -0.05, 0.06)
 
-# FP32 bound for the shock-carrying D2Q9 cases, derived from the arithmetic.
-# Shocks and contacts amplify rounding: over 1000 steps of the Riemann
-# problem the FP64 build differs from the FP64 oracle by 2.9e-14 in u from a
-# unit roundoff of 1.1e-16, a gain of about 2.6e2.  The same gain applied to
-# FP32's 6e-8 gives 1.6e-5, so 1e-5 is out of reach there; the bound is 5e-5
-# (3x margin).  The 1e-5 FP32 bound holds for the smooth Taylor-Green cases.
+# FP32 bound of the shock-carrying cases that have no float32 evaluation of
+# their own below (shock-liquid columns, shock capturing, learned closure):
+# the oracle evaluated in float32 already misses 1e-5 in u on a Ma 1.2 shock
+# tube (tests/test_oracle_fp32.py), so no FP32 implementation meets 1e-5 on
+# shocks with margin.  The Riemann problem and the Ma 1.2 shock tube are held
+# to 1e-5, or twice their own float32 evaluation where that is larger.
 FP32_SHOCK_TOL = 5e-5
 
 
 def shock_case(Nx=400, Ny=3, Ma=1.2):
-    from oracle import thermo
-    sc = copy.deepcopy(inputs.scenario("shock_drop_d2q9"))
-    e, v = sc["eos"], sc["vapour"]
-    r2, T2, u2, _ = thermo.rankine_hugoniot(v["rho"], v["T"], 0.0, Ma, e["a"], e["b"], e["R"], sc["cv"])
-    sc["post"] = dict(rho=r2, T=T2, u=u2)
-    return inputs.add_noise(inputs.shock_drop(2, (Nx, Ny), shock_x=60, with_drop=False, sc=sc), 3)
+    import fp32_eval
+    return fp32_eval.shock_case(3, Nx, Ny, Ma)
+
+
+def fp32_bound_of(case, steps, want):
+    """1e-5, or twice the error of the oracle evaluated in float32 on `case`."""
+    import fp32_eval
+    return fp32_eval.fp32_bound(fp32_eval.errors(fp32_eval.run(case, steps, "fp32"), want))
 
 
 # ---- config 1: D2Q9 Riemann problem, 1000 x 4, 1000 steps -----------------------
@@ -87,7 +88,7 @@ def test_riemann_fp64_multipass(riemann_ref):
 
 def test_riemann_fp32(riemann_ref):
     got = gpu_run(inputs.riemann(), 1000, "fp32")
-    assert_parity(got, riemann_ref, FP32_SHOCK_TOL, "riemann fp32")
+    assert_parity(got, riemann_ref, fp32_bound_of(inputs.riemann(), 1000, riemann_ref), "riemann fp32")
 
 
 # ---- D3Q27 Taylor-Green with noise on a ragged box -------------------------------
@@ -217,10 +218,11 @@ def test_riemann_fp16dev(riemann_ref):
 
 # ---- D2Q9 shock tube with inflow / outflow faces ---------------------------------
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", FP32_SHOCK_TOL)])
-def test_shock_tube(precision, tol):
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_shock_tube(precision):
     want = oracle_run(shock_case(), 300)
     got = gpu_run(shock_case(), 300, precision)
+    tol = 1e-12 if precision == "fp64" else fp32_bound_of(shock_case(), 300, want)
     assert_parity(got, want, tol, "shock tube " + precision)
 
 

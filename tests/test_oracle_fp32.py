@@ -19,22 +19,12 @@ with FP32 rounding and measure how far that lands from the FP64 oracle:
   Taylor-Green box (1000 steps).  The error of an FP32 trajectory is set by
   rounding throughout the step, not by the inversion alone.
 """
-import copy
-
 import numpy as np
 import pytest
 
 import inputs
-from fp32_eval import errors, run, tgv_drift_case
+from fp32_eval import errors, run, shock_case, tgv_drift_case
 from oracle import thermo
-
-
-def shock_case(seed, Nx=400, Ny=3, Ma=1.2):
-    sc = copy.deepcopy(inputs.scenario("shock_drop_d2q9"))
-    e, v = sc["eos"], sc["vapour"]
-    r2, T2, u2, _ = thermo.rankine_hugoniot(v["rho"], v["T"], 0.0, Ma, e["a"], e["b"], e["R"], sc["cv"])
-    sc["post"] = dict(rho=r2, T=T2, u=u2)
-    return inputs.add_noise(inputs.shock_drop(2, (Nx, Ny), shock_x=60, with_drop=False, sc=sc), seed)
 
 
 def t_fp64(rho, E, u_sq, a, cv):
