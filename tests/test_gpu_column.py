@@ -84,9 +84,19 @@ def test_column_fp64_matches_oracle_through_impact(P, name, make, steps64, steps
     assert_parity(gpu_run(P, make(), steps64, "fp64"), oracle_run(make(), steps64), 1e-12, name + " fp64")
 
 
+# Per-node bound of the FP32 column runs: the liquid column is at rest before
+# the impact, so u vanishes to rounding at every liquid node and FP32 rounding
+# picks the side of Phi's upwind difference there (Sec. 3.2; reading 21 of the
+# design notes: in the oracle a 1e-7 perturbation moves the fields by 2e-3
+# after the impact).  Single nodes move by up to about 1e-2 x rms(u) (measured
+# 4.1e-3 in 3-D, 1.0e-3 in 2-D) while the norm stays inside the bound.
+COLUMN_NODE_MULT = 200.0
+
+
 @pytest.mark.parametrize("name,make,steps64,steps32", CASES, ids=[c[0] for c in CASES])
 def test_column_fp32_matches_oracle_before_impact(P, name, make, steps64, steps32):
-    assert_parity(gpu_run(P, make(), steps32, "fp32"), oracle_run(make(), steps32), FP32_SHOCK_TOL, name + " fp32")
+    assert_parity(gpu_run(P, make(), steps32, "fp32"), oracle_run(make(), steps32), FP32_SHOCK_TOL, name + " fp32",
+                  node_mult=COLUMN_NODE_MULT)
 
 
 def test_column_multipass_and_graphs_match_fused(P):
