@@ -522,7 +522,7 @@ def run_ours(args):
     closure_info, net = None, None
     if args.workload in MLP_WORKLOADS:
         # same case with the exact closure first: tuned, then timed like the main loop
-        net, closure_info = train_closure(P, dev, args.workload)
+        net, closure_info = train_closure(P, dev, args.workload, args.train_mma)
         if not args.no_autotune:
             P.lbm_autotune(solver.h, 3)
         P.lbm_step(solver.h, args.warmup)
@@ -678,25 +678,35 @@ def run_ours(args):
     return 0
 
 
-def train_closure(P, dev, workload):
-    """Train the learned closure on solver states (GPU), untimed; returns (net, info)."""
+def train_closure(P, dev, workload, mma="tcgen05"):
+    """Train the learned closure on solver states (GPU), outside the timed region; returns (net, info).
+    The AdamW steps are timed with CUDA events on the network's stream (the current stream)."""
     import numpy as np
     import torch
     import inputs
     t0 = time.perf_counter()
     table, Ma_max, units, columns = MLP_WORKLOADS[workload]
     sc = inputs.scenario(units)
-    net = P.Closure(sc["eos"]["a"], sc["eos"]["b"], sc["eos"]["R"], sc["cv"], seed=MLP_TRAIN["net_seed"])
+    net = P.Closure(sc["eos"]["a"], sc["eos"]["b"], sc["eos"]["R"], sc["cv"], seed=MLP_TRAIN["net_seed"],
+                    stream=torch.cuda.current_stream(dev).cuda_stream)
+    net.mma = P.LBM_MLP_MMA_TCGEN05 if mma == "tcgen05" else P.LBM_MLP_MMA_WARP
     runs = inputs.closure_training_runs(table=table, Ma_max=Ma_max, columns=columns)
     rho, e = net.collect_runs(runs, MLP_TRAIN["snapshots"],
                               MLP_TRAIN["every"], precision="fp32", shock_capturing=SC_WORKLOADS.get(workload))
     net.fit_scaling(rho, e)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
     losses = net.train(rho, e, batch=MLP_TRAIN["batch"], steps=MLP_TRAIN["steps"], lr0=MLP_TRAIN["lr0"],
                        lr1=MLP_TRAIN["lr1"], seed=MLP_TRAIN["seed"])
+    e1.record()
     torch.cuda.synchronize(dev)
+    train_ms = e0.elapsed_time(e1)
     info = {"kind": "mlp 2-64-64-3, bf16 weights, fp32 accumulate, range-gated exact fallback",
             "train_samples": int(rho.numel()), "train_steps": MLP_TRAIN["steps"], "batch": MLP_TRAIN["batch"],
-            "final_loss": float(np.mean(losses[-100:])), "train_and_collect_s": time.perf_counter() - t0}
+            "final_loss": float(np.mean(losses[-100:])), "train_and_collect_s": time.perf_counter() - t0,
+            "train_contraction": mma, "train_s": train_ms / 1e3,
+            "train_us_per_step": 1e3 * train_ms / max(1, MLP_TRAIN["steps"])}
     del rho, e
     return net, info
 
@@ -720,6 +730,8 @@ def main():
                     help="replay captured CUDA graphs (lbm_set_graphs); each chunk is timed as a whole")
     ap.add_argument("--train-steps", type=int, default=None,
                     help="AdamW steps of the learned closure (learned-closure workloads)")
+    ap.add_argument("--train-mma", default="tcgen05", choices=["tcgen05", "warp"],
+                    help="contraction path of the closure training (lbm_mlp_set_mma)")
     args = ap.parse_args()
     if args.train_steps is not None:
         MLP_TRAIN["steps"] = args.train_steps

@@ -91,6 +91,23 @@ int lbm_mlp_set_params(lbm_mlp_t net, const float* theta);
  * weights).  1 <= n <= 2^20. */
 int lbm_mlp_loss_grad(lbm_mlp_t net, const float* x, const float* y, int n, double* loss, float* grad);
 
+/* Contraction path of the training kernels.  LBM_MLP_MMA_TCGEN05 (the
+ * default): one kernel takes the minibatch through forward pass, backward
+ * pass and all weight gradients on the fifth-generation tensor cores
+ * (tcgen05.mma, BF16 x BF16 -> FP32 accumulators in tensor memory, groups of
+ * 128 samples), every FP32 operand split into two bfloat16 terms, so all
+ * gradients are at the FP32 level.  LBM_MLP_MMA_WARP: warp-level mma.sync
+ * m16n8k16 for the 64 x 64 products, with dL/dz2 rounded to bfloat16 in dW2
+ * and in the input gradient of layer 2 (relative error about 1e-3 there).
+ * A tensor-core completion wait that runs out makes lbm_mlp_loss_grad and
+ * lbm_mlp_train return LBM_ECUDA.
+ * Errors: LBM_EINVAL (NULL network, unknown kind). */
+#define LBM_MLP_MMA_WARP 0
+#define LBM_MLP_MMA_TCGEN05 1
+int lbm_mlp_set_mma(lbm_mlp_t net, int kind);
+/* The contraction path in use (LBM_MLP_MMA_*). */
+int lbm_mlp_get_mma(lbm_mlp_t net);
+
 /* `steps` AdamW steps (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight
  * decay wd) on minibatches of `batch` samples drawn uniformly with
  * replacement from the n device samples (d_rho, d_e), index k of step t from

@@ -48,7 +48,8 @@ EXPORTS = ("lbm_create", "lbm_set_boundary", "lbm_set_stream", "lbm_init", "lbm_
            # include/lbm_mlp.h
            "lbm_mlp_create", "lbm_mlp_set_stream", "lbm_mlp_collect", "lbm_mlp_fit_scaling", "lbm_mlp_get_scaling",
            "lbm_mlp_set_scaling", "lbm_mlp_get_params", "lbm_mlp_set_params", "lbm_mlp_loss_grad", "lbm_mlp_train",
-           "lbm_mlp_predict", "lbm_mlp_attach", "lbm_get_closure", "lbm_mlp_destroy", "lbm_mlp_last_error")
+           "lbm_mlp_predict", "lbm_mlp_attach", "lbm_get_closure", "lbm_mlp_destroy", "lbm_mlp_last_error",
+           "lbm_mlp_set_mma", "lbm_mlp_get_mma")
 LBM_MLP_NPARAM, LBM_MLP_NSCALE = 4547, 10
 
 
@@ -141,6 +142,8 @@ def load():
         "lbm_mlp_attach": (I, [P, P]),
         "lbm_get_closure": (I, [P]),
         "lbm_mlp_destroy": (I, [P]),
+        "lbm_mlp_set_mma": (I, [P, I]),
+        "lbm_mlp_get_mma": (I, [P]),
         "lbm_mlp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -541,6 +544,18 @@ def lbm_get_closure(h):
     return load().lbm_get_closure(h)
 
 
+LBM_MLP_MMA_WARP, LBM_MLP_MMA_TCGEN05 = 0, 1
+
+
+def lbm_mlp_set_mma(net, kind):
+    """Contraction path of the training kernels (LBM_MLP_MMA_TCGEN05 default, or LBM_MLP_MMA_WARP)."""
+    _mcheck(load().lbm_mlp_set_mma(net, int(kind)))
+
+
+def lbm_mlp_get_mma(net):
+    return int(load().lbm_mlp_get_mma(net))
+
+
 def lbm_mlp_destroy(net):
     return load().lbm_mlp_destroy(net)
 
@@ -653,6 +668,15 @@ class Closure:
     @params.setter
     def params(self, theta):
         lbm_mlp_set_params(self.net, theta)
+
+    @property
+    def mma(self):
+        """Contraction path of training: LBM_MLP_MMA_TCGEN05 or LBM_MLP_MMA_WARP."""
+        return lbm_mlp_get_mma(self.net)
+
+    @mma.setter
+    def mma(self, kind):
+        lbm_mlp_set_mma(self.net, kind)
 
     def loss_grad(self, x, y):
         return lbm_mlp_loss_grad(self.net, x, y)

@@ -54,22 +54,45 @@ def test_initial_weights_match_oracle(P):
     net.close()
 
 
-@pytest.mark.parametrize("n", [1, 37, 1000, 4099])
-def test_loss_and_gradient_match_oracle(P, n):
-    net = make_net(P)
-    th = perturbed_params(5)
+# tolerances (relative L2) of the gradient against the FP64 oracle on the same
+# bfloat16 weights.  Warp form: FP32 paths for b2, W3, b3; bfloat16-rounded
+# dL/dz2 in dW2 and in the input gradient of layer 2 (W1, b1).  Tensor-core
+# form: every product takes its FP32 operands as bfloat16 hi + lo, so all
+# gradients are at the FP32 level.
+GRAD_TOL = {"warp": dict(W1=1e-2, b1=1e-2, W2=1e-2, b2=1e-4, W3=1e-4, b3=1e-4),
+            "tcgen05": dict(W1=1e-4, b1=1e-4, W2=1e-4, b2=1e-4, W3=1e-4, b3=1e-4)}
+
+
+def check_loss_and_gradient(P, net, mma, n, seed):
+    net.mma = P.LBM_MLP_MMA_TCGEN05 if mma == "tcgen05" else P.LBM_MLP_MMA_WARP
+    th = perturbed_params(seed)
     net.params = th
-    X = np.stack([inputs.uniform(7, n), inputs.uniform(8, n)], axis=1).astype(np.float32)
+    X = np.stack([inputs.uniform(seed + 2, n), inputs.uniform(seed + 3, n)], axis=1).astype(np.float32)
     Y = np.stack([np.sin(2 * X[:, 0]) * X[:, 1], X[:, 0] ** 2 - 0.3, np.cos(X[:, 1])], axis=1).astype(np.float32)
     loss, g = net.loss_grad(X, Y)
     lo, go = mlp.loss_and_grad(mlp.quantize(th), X.astype(np.float64), Y.astype(np.float64))
     assert abs(loss - lo) <= 1e-5 * lo, (loss, lo)
     gp, op = mlp.unpack(g), mlp.unpack(go)
-    # FP32 paths: b2, W3, b3; bf16-rounded dL/dz2 in dW2 and in the input gradient of layer 2
-    tol = dict(W1=1e-2, b1=1e-2, W2=1e-2, b2=1e-4, W3=1e-4, b3=1e-4)
     for name, _ in mlp.SHAPES:
         err = rel_l2(gp[name], op[name])
-        assert err <= tol[name], (name, err)
+        assert err <= GRAD_TOL[mma][name], (mma, name, err)
+
+
+@pytest.mark.parametrize("mma", ["tcgen05", "warp"])
+@pytest.mark.parametrize("n", [1, 37, 1000, 4099])
+def test_loss_and_gradient_match_oracle(P, n, mma):
+    net = make_net(P)
+    check_loss_and_gradient(P, net, mma, n, 5)
+    net.close()
+
+
+@pytest.mark.parametrize("n", [128, 129, 19457, 60001])
+def test_tensor_core_gradient_over_many_groups(P, n):
+    """Full and ragged groups of 128 samples; above 152 groups a block
+    accumulates several groups in tensor memory."""
+    net = make_net(P)
+    assert net.mma == P.LBM_MLP_MMA_TCGEN05                 # the default path
+    check_loss_and_gradient(P, net, "tcgen05", n, 11)
     net.close()
 
 
