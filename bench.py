@@ -658,6 +658,7 @@ def run_ours(args):
             em = closure_info["exact_closure_ms_per_step"]
             closure_info["exact_closure_mlups"] = N / (em * 1e-3) / 1e6
             closure_info["gain_vs_exact"] = value / world / closure_info["exact_closure_mlups"]
+            closure_info["accuracy"] = closure_accuracy(P, net, args.workload)
             line["closure"] = closure_info
         if not args.no_cpu:
             # the oracle on the host cores; its single-core run's final fields give the
@@ -676,6 +677,45 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+CLOSURE_ACCURACY_STEPS = 400
+
+
+def closure_accuracy(P, net, workload):
+    """Density error of the learned closure in FP32, beside that of the exact closure in FP32, against the exact
+    closure in FP64 (relative L2 after CLOSURE_ACCURACY_STEPS steps), on the workload at half its size in every
+    direction (the same fluid, shock and shock capturing); outside the timed region."""
+    import numpy as np
+    import inputs
+    builder, kw, _, _ = WORKLOADS[workload]
+    kw = dict(kw)
+    kw["shape"] = tuple(n // 2 for n in kw["shape"])
+    if "radius" in kw:
+        kw["radius"] = kw["radius"] // 2
+    case = getattr(inputs, builder)(**kw)
+    sc = SC_WORKLOADS.get(workload)
+
+    def density(prec, learned):
+        s = P.Solver(case, precision=prec)
+        if sc:
+            P.lbm_set_shock_capturing(s.h, *sc)
+        s.init()
+        if learned:
+            net.attach(s)
+        s.step(CLOSURE_ACCURACY_STEPS)
+        rho = np.asarray(s.fields()["rho"], dtype=np.float64)
+        s.close()
+        return rho
+
+    ref = density("fp64", False)
+
+    def rel(a):
+        return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+    return {"case": "x".join(str(n) for n in kw["shape"]) + (", radius %d" % kw["radius"] if "radius" in kw else ""),
+            "steps": CLOSURE_ACCURACY_STEPS, "reference": "exact closure, FP64",
+            "rho_rel_l2_learned_fp32": rel(density("fp32", True)),
+            "rho_rel_l2_exact_fp32": rel(density("fp32", False)), "bar": 1e-3}
 
 
 def train_closure(P, dev, workload, mma="tcgen05"):
