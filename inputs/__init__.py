@@ -200,13 +200,22 @@ def batch(n=None):
     return cases
 
 
-def slab(T_r=0.95, Nx=256, kappa=None, width=3.0):
+def coexistence_state(T_r):
+    """The coexistence_d2q9 table's entry for reduced temperature T_r."""
+    states = scenario("coexistence_d2q9")["states"]
+    for k, st in states.items():
+        if abs(float(k) - T_r) < 1e-9:
+            return st
+    raise KeyError("no coexistence state at T_r %r (table: %s)" % (T_r, ", ".join(states)))
+
+
+def slab(T_r=0.95, Nx=256, kappa=None, width=3.0, state=None):
     """Periodic D2Q9 slab (coexistence_d2q9): saturated liquid between x = Nx/4 and
-    3 Nx/4 in its saturated vapour at reduced temperature T_r (one of the table's),
-    tanh interfaces of `width` nodes, at rest, one node along y.  kappa: lattice
-    capillarity (default the table's)."""
+    3 Nx/4 in its saturated vapour at reduced temperature T_r (one of the table's,
+    or `state`: an entry of the same form), tanh interfaces of `width` nodes, at
+    rest, one node along y.  kappa: lattice capillarity (default the table's)."""
     tab = scenario("coexistence_d2q9")
-    st = tab["states"]["%.2f" % T_r]
+    st = coexistence_state(T_r) if state is None else state
     eos = dict(st["eos"])
     if kappa is not None:
         eos["kappa"] = kappa

@@ -258,6 +258,11 @@ def batch(n=256, seed=2025, Ma_lo=1.1, Ma_hi=1.3):
     return dict(base="shock_drop_d2q9", instances=out)
 
 
+def coexistence_key(T_r):
+    """Table key of a reduced temperature: two decimals, three where needed (0.845)."""
+    return "%.2f" % T_r if abs(round(T_r, 2) - T_r) < 1e-12 else "%.3f" % T_r
+
+
 def coexistence(T_r=(0.85, 0.9, 0.95, 0.99), nu=0.01, kappa=0.1):
     """Flat liquid-vapour equilibria (Sec. "Liquid-vapour co-existence"): for each
     reduced temperature the Maxwell densities (the reference the paper compares
@@ -265,14 +270,18 @@ def coexistence(T_r=(0.85, 0.9, 0.95, 0.99), nu=0.01, kappa=0.1):
     vapour.  U^2 follows the liquid rule of shock_column (c_s^2(liquid) / U^2 <=
     0.175; theta / U^2 <= 1/4); lattice viscosity nu, kappa the default lattice
     capillarity (the interface spans about 2 sqrt(kappa / a) / sqrt(1 - T_r)
-    nodes).  Below T_r ~ 0.85 the slab does not run in this scheme."""
+    nodes).  Below T_r = 27/32 the van der Waals pressure is negative inside the
+    interface (the isotherm's minimum crosses zero there), so theta = P / rho and
+    tau = mu / P are negative at the first step and the slab cannot run.  At 0.845
+    (minimum interface pressure 0.010) a 256-node slab's relaxation, which lowers
+    its temperature by about 1e-3, still reaches P <= 0; 0.85 (0.050) runs."""
     out = {}
     for Tr in T_r:
         rl, rv = thermo.maxwell_coexistence(Tr, A_R, B, R_GAS)
         cs2_l = thermo.sound_speed_sq(rl, Tr, A_R, B, R_GAS, CV)
         U2 = float(max(math.ceil(cs2_l / 0.175), _u2_for([(rl, Tr), (rv, Tr)])))
         eos = _lattice_eos(U2, kappa=kappa, eta_over_mu=1.0, rho_ref=rv, T_ref_r=Tr)
-        out["%.2f" % Tr] = dict(U2=U2, eos=eos, tau=_tau(eos, nu), rho_l=rl, rho_v=rv, T=Tr / U2)
+        out[coexistence_key(Tr)] = dict(U2=U2, eos=eos, tau=_tau(eos, nu), rho_l=rl, rho_v=rv, T=Tr / U2)
     return dict(D=2, cv=CV, Pr=0.71, nu=nu, T_r=list(T_r), states=out)
 
 

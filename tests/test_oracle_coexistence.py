@@ -30,3 +30,60 @@ def test_slab_plateaus_reach_maxwell_coexistence():
     dl, dv = slab_plateaus()
     assert abs(dl) < 0.01, dl
     assert abs(dv) < 0.02, dv
+
+
+# ---- the range of the scheme: the sign of the pressure inside the interface ----
+# theta = P / rho (Eq. theta) and tau = mu / P must be positive.  Every density
+# between the vapour and the liquid occurs inside the interface, and below
+# T_r = 27/32 the van der Waals isotherm dips below zero pressure there.
+
+A_R, B_R, R_R = 3.0, 1.0 / 3.0, 8.0 / 3.0            # reduced van der Waals
+
+
+def test_isotherm_minimum_touches_zero_at_27_over_32():
+    """Closed form: P_r = 8 T / (3 v - 1) - 3 / v^2 has P = 0 and dP/dv = 0 together only
+    at v = 2/3, T = 27/32 (rho_r = 3/2): the two conditions give 3/(3v - 1) = 2/v."""
+    T, rho = 27.0 / 32.0, 1.5
+    assert abs(thermo.pressure(rho, T, A_R, B_R, R_R)) < 1e-14
+    h = 1e-4
+    dP = (thermo.pressure(rho + h, T, A_R, B_R, R_R) - thermo.pressure(rho - h, T, A_R, B_R, R_R)) / (2 * h)
+    assert abs(dP) < 1e-7, dP
+    assert thermo.pressure(rho + 0.05, T, A_R, B_R, R_R) > 0 and thermo.pressure(rho - 0.05, T, A_R, B_R, R_R) > 0
+
+
+def interface_min_pressure(T_r):
+    rl, rv = thermo.maxwell_coexistence(T_r, A_R, B_R, R_R)
+    rho = np.linspace(rv, rl, 20001)
+    return thermo.pressure(rho, T_r, A_R, B_R, R_R).min()
+
+
+def test_interface_pressure_changes_sign_at_27_over_32():
+    assert interface_min_pressure(0.845) > 0.009
+    assert interface_min_pressure(27.0 / 32.0 + 1e-4) > 0
+    assert interface_min_pressure(27.0 / 32.0 - 1e-4) < 0
+    assert interface_min_pressure(0.84) < -0.03
+
+
+def oracle_slab(T_r, Nx=64):
+    from oracle import write_scenarios as ws
+    st = ws.coexistence(T_r=(T_r,))["states"][ws.coexistence_key(T_r)]
+    c = inputs.slab(T_r, Nx, state=st)
+    m = lbm.Model(c.D, c.shape, c.eos, c.tau, c.Pr, c.cv, c.x_low, c.x_high)
+    return c, lbm.Sim(m, c.rho, c.u, c.T)
+
+
+def test_slab_below_27_over_32_has_negative_theta_in_its_interface():
+    """At T_r 0.84 the first step leaves interface nodes with P < 0 (theta, tau < 0); at
+    T_r 0.85 (the table's lowest entry) the pressure stays positive everywhere."""
+    for T_r, steps in ((0.84, 1), (0.85, 1000)):
+        c, s = oracle_slab(T_r)
+        F = s.step(steps).fields()
+        r, T = F["rho"][0], F["T"][0]
+        P = thermo.pressure(r, T * 1.0, c.eos["a"], c.eos["b"], c.eos["R"])
+        if T_r < 27.0 / 32.0:
+            bad = np.where(P < 0)[0]
+            assert bad.size > 0
+            # inside the interfaces (tanh centres at Nx/4 and 3 Nx/4), not in the plateaus
+            assert all(min(abs(i - 16), abs(i - 48)) <= 6 for i in bad), bad
+        else:
+            assert np.isfinite(r).all() and (P > 0).all(), P.min()
