@@ -382,6 +382,7 @@ int lbm_create(lbm_t* out, int lattice, int Nx, int Ny, int Nz, const lbm_eos* e
     cp = cvr + T * dPdT * dPdT / (r * r * dPdr);
   }
   p.k_over_mu = cp / Pr;                                   // Pr = mu c_p / k
+  set_model_fp32(p);
   m = host_model(*h);
   if (h->precision == LBM_FP16DEV) {
     double feq[27], geq[27], u0[3] = {0, 0, 0};

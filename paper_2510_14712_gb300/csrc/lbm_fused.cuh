@@ -155,13 +155,29 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
   return v < 0 ? -v : (v >= T ? v - T + 1 : 0);
 }
 
+// Options of the fused step (template bit mask).
+//   kOptRows: stage A in row form (3-D; FP32 or FP16-deviation storage; x
+//     periodic with Nx a multiple of 4; not SMALL): the R3 box is cut into
+//     rows of TX + 8 nodes that start 4 nodes left of the tile, and each row
+//     into chunks of 4 nodes, one chunk per lane.  A lane reads the 4 values of
+//     one direction with one 16-byte (FP16: 8-byte) load of the source row
+//     (aligned: x0 and Nx are multiples of 4, so a chunk never straddles the
+//     periodic seam), and the value a node pulls from across the chunk edge
+//     comes from the neighbouring lane by a shuffle.  Warps take groups of
+//     whole rows: the f rows of the R3 box (rho; j on the R1 rows), then the
+//     g rows of the R1 box (S).  Per node and direction the moments are summed
+//     in the same order as the position form, so both give the same bits.
+//     Stage D's in-plane pull offsets are computed once per work item (the
+//     thread's node is the same on every plane).
+constexpr int kOptRows = 1;
+
 // One (column, z-segment) work item of the fused step: all planes mb..me-1 of
 // the column of TX x hy nodes at (x0, y0) (hy <= TY rows; 1 in 2-D), reading A
 // and writing B.  Shared by the single-instance kernel and the batched
 // persistent kernel.  SMALL: the box is narrower than a tile plus its halo in
 // x or y, so coordinates need an exact modulo instead of a single conditional
 // wrap.
-template <int D, typename S, typename real, int TX, int TY, bool SMALL, class CL>
+template <int D, typename S, typename real, int TX, int TY, bool SMALL, class CL, int OPT = 0>
 __device__ __forceinline__ void fused_column(const Params& p, const typename Store<S>::T* __restrict__ A,
                                              typename Store<S>::T* __restrict__ B, int x0, int y0, int hy, int mb,
                                              int me, unsigned char* smem_raw, unsigned& flags, const CL& closure) {
@@ -186,8 +202,143 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   // element offsets inside a population buffer fit 32 bits (checked at create)
   const unsigned plane32 = unsigned(p.plane), pitch32 = unsigned(p.pitch);
 
+  constexpr bool kRows = (OPT & kOptRows) != 0 && D == 3 && !SMALL && sizeof(real) == 4;
+  constexpr bool kItem = kRows;
+  // stage D's in-plane pull offsets of this thread's node (kItem)
+  unsigned dxc[3], dyr[3];
+  if constexpr (kItem) {
+    const int dgx = x0 + tid % TX, dgy = y0 + tid / TX;
+#pragma unroll
+    for (int c = -1; c <= 1; ++c) {
+      dxc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(dgx - c, p.Nx) : dgx + p.G - c);
+      dyr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(dgy - c, p.Ny)) * pitch32 : 0u;
+    }
+  }
+
   for (int pl = mb - 3; pl <= me + 2; ++pl) {
     // ---------------- A: moments of plane pl --------------------------------
+    if constexpr (kRows) {
+      constexpr int NCH = (TX + 8) / 4, RPW = 32 / NCH;
+      static_assert(TX % 4 == 0 && RPW >= 1, "row form: TX + 8 nodes in 4-node chunks, at least one row per warp");
+      const int slot = (pl + 6) % 3;
+      const int mp = modp(pl, Nm);
+      const ST* Pm[3];
+#pragma unroll
+      for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
+      const int lane = tid & 31, rr = lane / NCH, ch = lane - rr * NCH;
+      // Row groups of three kinds: f rows of the R1 box (rho and j), g rows of
+      // the R1 box (S), and the four f rows of the R3 box outside it (rho
+      // only).  Warps take groups in snake order (w, 2 nw - 1 - w, 2 nw + w,
+      // ...), so that the warps given a second group hold the cheap ones.
+      const int n1 = hy + 2 * G::HY1;                                   // rows of the R1 box
+      const int g1 = (n1 + RPW - 1) / RPW, g3 = (4 + RPW - 1) / RPW;
+      const int ngroups = 2 * g1 + g3, nw = G::NT / 32, w = tid >> 5;
+      int xs = x0 - 4 + 4 * ch;                                         // first node of the chunk
+      xs += xs < 0 ? p.Nx : 0;
+      xs -= xs >= p.Nx ? p.Nx : 0;
+      for (int k = 0;; ++k) {
+        const int gi = (k & 1) ? (k + 1) * nw - 1 - w : k * nw + w;
+        if (gi >= ngroups) break;
+        const int kind = gi < g1 ? 0 : (gi < 2 * g1 ? 1 : 2);          // warp-uniform
+        const int r = (gi - (kind == 0 ? 0 : (kind == 1 ? g1 : 2 * g1))) * RPW + rr;
+        const bool act = rr < RPW && r < (kind == 2 ? 4 : n1);
+        // row of the R3 box
+        const int ly = kind == 2 ? (r < 2 ? r : hy + 2 + r) : r + (G::HY3 - G::HY1);
+        const int gy = y0 + ly - G::HY3;
+        unsigned ro[3];
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) ro[c + 1] = unsigned(wrapc<false>(act ? gy - c : y0, p.Ny)) * pitch32 + xs;
+        // the four nodes' values of direction i, as pulled: element j of the
+        // chunk, or of the chunk left / right of it (neighbouring lane)
+        auto pulled = [&](const int i, const int ii, real* w) {
+          const int cx = L::c(i, 0), cy = L::c(i, 1), cm = L::c(i, 2);
+          const unsigned o = unsigned(ii) * plane32 + ro[cy + 1];
+          // every lane loads (idle lanes read a valid chunk of row y0 whose
+          // values no active lane takes), so the loads need no predicate
+          real v[4];
+          if (pop_ok(p, Pm[cm + 1], o, 4)) Store<S>::template ld4<real>(Pm[cm + 1], o, p.ref[ii], v);
+          else v[0] = v[1] = v[2] = v[3] = real(0);
+          if (cx == 1) {
+            w[0] = __shfl_up_sync(0xffffffffu, v[3], 1);
+            w[1] = v[0]; w[2] = v[1]; w[3] = v[2];
+          } else if (cx == -1) {
+            w[0] = v[1]; w[1] = v[2]; w[2] = v[3];
+            w[3] = __shfl_down_sync(0xffffffffu, v[0], 1);
+          } else {
+            w[0] = v[0]; w[1] = v[1]; w[2] = v[2]; w[3] = v[3];
+          }
+        };
+        if (kind == 0) {
+          real rho[4], sp[D][4], sn[D][4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            rho[j] = real(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) sp[a][j] = sn[a][j] = real(0);
+          }
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            real w[4];
+            pulled(i, i, w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              rho[j] += w[j];
+#pragma unroll
+              for (int a = 0; a < D; ++a) {
+                if (L::c(i, a) == 1) sp[a][j] += w[j];
+                if (L::c(i, a) == -1) sn[a][j] += w[j];
+              }
+            }
+          }
+          if (act) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int lx = 4 * ch + j - 1;                            // x index in the R3 box
+              if (lx >= 0 && lx < G::BX3) s_rho[slot * G::N3 + ly * G::BX3 + lx] = rho[j];
+              const int lx1 = lx - 2;                                   // x index in the R1 box
+              if (lx1 >= 0 && lx1 < G::BX1) {
+                real* dst = s_mom + (slot * G::NMOM) * G::N1 + (ly - (G::HY3 - G::HY1)) * G::BX1 + lx1;
+#pragma unroll
+                for (int a = 0; a < D; ++a) dst[a * G::N1] = sp[a][j] - sn[a][j];
+              }
+            }
+          }
+        } else if (kind == 2) {
+          real rho[4] = {real(0), real(0), real(0), real(0)};
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            real w[4];
+            pulled(i, i, w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) rho[j] += w[j];
+          }
+          if (act) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int lx = 4 * ch + j - 1;
+              if (lx >= 0 && lx < G::BX3) s_rho[slot * G::N3 + ly * G::BX3 + lx] = rho[j];
+            }
+          }
+        } else {
+          real Se[4] = {real(0), real(0), real(0), real(0)};
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            real w[4];
+            pulled(i, Q + i, w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Se[j] += w[j];
+          }
+          if (act) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int lx1 = 4 * ch + j - 3;
+              if (lx1 >= 0 && lx1 < G::BX1) s_mom[(slot * G::NMOM + D) * G::N1 + r * G::BX1 + lx1] = Se[j];
+            }
+          }
+        }
+      }
+    } else
+    // Position form.
     // Direction-outer loop over this thread's positions of the R3 box: three
     // per-plane base pointers and one 32-bit element offset per load
     // (direction * plane + row + column).  j_a is accumulated as (sum over
@@ -379,8 +530,13 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 #pragma unroll
         for (int c = -1; c <= 1; ++c) {
           Pm[c + 1] = A + (long long)wrap(mq - c, Nm) * mstride;
-          xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
-          yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
+          if constexpr (kItem) {
+            xc[c + 1] = dxc[c + 1];
+            yr[c + 1] = dyr[c + 1];
+          } else {
+            xc[c + 1] = unsigned(p.periodic_x ? wrapc<SMALL>(gx - c, p.Nx) : gx + p.G - c);
+            yr[c + 1] = D == 3 ? unsigned(wrapc<SMALL>(gy - c, p.Ny)) * pitch32 : 0u;
+          }
         }
         ST* Bq = B + (long long)mq * mstride;
         const int k1 = (ly + G::HY1) * G::BX1 + (lx + 1);
@@ -473,7 +629,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
 // CTA slots).  MINB: CTAs per SM
 // the register allocation must allow (2 keeps one CTA's memory phase
 // overlapping the other's collision).
-template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL, class CL = ExactClosure<real>>
+template <int D, typename S, typename real, int TX, int TY, int MINB, bool SMALL, class CL = ExactClosure<real>,
+          int OPT = 0>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __restrict__ A,
              typename Store<S>::T* __restrict__ B, unsigned* err, int ncolx, int ncoly, int nseg) {
@@ -494,7 +651,7 @@ k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __res
     const int band = col / ncolx;
     const int y0 = D == 3 ? int((long long)p.Ny * band / ncoly) : 0;
     const int hy = D == 3 ? int((long long)p.Ny * (band + 1) / ncoly) - y0 : 1;
-    fused_column<D, S, real, TX, TY, SMALL, CL>(p, A, B, x0, y0, hy, mb, me, smem_raw, flags, closure);
+    fused_column<D, S, real, TX, TY, SMALL, CL, OPT>(p, A, B, x0, y0, hy, mb, me, smem_raw, flags, closure);
   }
   if (flags) atomicOr(err, flags);
 }

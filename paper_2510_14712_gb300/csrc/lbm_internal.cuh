@@ -49,9 +49,13 @@ struct Params {
   // the handle's two population buffers (2 Q plane elements each): the
   // bounds of every population access in bounds-check builds
   const void* pop[2];
+  // the model constants above rounded to FP32 once on the host (set_model_fp32),
+  // so that FP32 kernels read them as they are instead of converting the FP64
+  // copies (a conversion the compiler may repeat inside loops, on the FP64 pipe)
+  Model<float> mf;
 };
 
-template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
+template <typename real> __host__ __device__ inline Model<real> model_convert(const Params& p) {
   Model<real> m;
   m.a = real(p.a); m.b = real(p.b); m.R = real(p.R); m.cv = real(p.cv);
   m.kappa = real(p.kappa); m.eta_over_mu = real(p.eta_over_mu);
@@ -59,6 +63,15 @@ template <typename real> __host__ __device__ inline Model<real> model_of(const P
   m.kind = p.eos_kind; m.Tc = real(p.Tc); m.mpr = real(p.mpr);
   return m;
 }
+
+// model constants in the arithmetic type
+template <typename real> __host__ __device__ inline Model<real> model_of(const Params& p) {
+  if constexpr (sizeof(real) == 4) return p.mf;
+  else return model_convert<real>(p);
+}
+
+// fill Params::mf from the FP64 constants (after every change of them)
+inline void set_model_fp32(Params& p) { p.mf = model_convert<float>(p); }
 
 // One solver instance.
 struct Handle {

@@ -38,6 +38,11 @@ template <> struct Store<float> {
   template <typename real, typename I> __device__ static real ld_last(const T* p, I o, float) { return real(__ldcs(p + o)); }
   template <typename real, typename I> __device__ static void st(T* p, I o, real v, float) { p[o] = float(v); }
   template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float) { __stcs(p + o, float(v)); }
+  // four consecutive values p[o .. o+3], o a multiple of 4 (one 16-byte load)
+  template <typename real, typename I> __device__ static void ld4(const T* p, I o, float, real* v) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p + o));
+    v[0] = real(q.x); v[1] = real(q.y); v[2] = real(q.z); v[3] = real(q.w);
+  }
 };
 template <> struct Store<Fp16Dev> {
   using T = __half;
@@ -52,6 +57,13 @@ template <> struct Store<Fp16Dev> {
   }
   template <typename real, typename I> __device__ static void st_stream(T* p, I o, real v, float ref) {
     __stcs(p + o, __float2half_rn(float(v) - ref));
+  }
+  // four consecutive values p[o .. o+3], o a multiple of 4 (one 8-byte load)
+  template <typename real, typename I> __device__ static void ld4(const T* p, I o, float ref, real* v) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p + o));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    v[0] = real(a.x + ref); v[1] = real(a.y + ref); v[2] = real(b.x + ref); v[3] = real(b.y + ref);
   }
 };
 

@@ -42,12 +42,12 @@ template <int D, typename S, typename real> struct OpsImpl {
 
   // One tile shape of the fused kernel (TX x TY in-plane nodes, MINB CTAs
   // per SM for the register budget) with thermodynamic closure CL.
-  template <int TX, int TY, int MINB, class CL> struct Fused {
+  template <int TX, int TY, int MINB, class CL, int OPT = 0> struct Fused {
     using FG = FusedGeom<D, TX, TY, CL::kExtra>;
     static size_t smem() { return FG::template smem_bytes<real>() + CL::kSmem; }
     struct Launch {
       int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
-      bool small = false;
+      bool small = false, rows = false;
     };
     // One CTA per (column, z-segment), never more items than resident CTA
     // slots so that all run together.  In 3-D the plane is cut into ncolx
@@ -61,9 +61,11 @@ template <int D, typename S, typename real> struct OpsImpl {
     static Launch plan(const Params& p) {
       static int blocks_per_sm = -1, sms = 0;
       if (blocks_per_sm < 0) {
-        auto kern = k_step_fused<D, S, real, TX, TY, MINB, false, CL>;
-        auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true, CL>;
+        auto kern = k_step_fused<D, S, real, TX, TY, MINB, false, CL, OPT>;
+        auto kern_pos = k_step_fused<D, S, real, TX, TY, MINB, false, CL, OPT & ~kOptRows>;
+        auto kern_small = k_step_fused<D, S, real, TX, TY, MINB, true, CL, OPT & ~kOptRows>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        cudaFuncSetAttribute(kern_pos, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         cudaFuncSetAttribute(kern_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, FG::NT, smem());
         int dev = 0;
@@ -97,13 +99,16 @@ template <int D, typename S, typename real> struct OpsImpl {
       if (g > slots) g = slots;
       l.grid = int(g);
       l.small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
+      // row form of stage A: aligned 4-node chunks of periodic rows
+      l.rows = (OPT & kOptRows) && D == 3 && sizeof(real) == 4 && !l.small && p.periodic_x && p.Nx % 4 == 0;
       return l;
     }
     static void launch(Handle& h, const void* src, void* dst) {
       const Params& p = h.p;
       const Launch l = plan(p);
-      auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true, CL>
-                          : k_step_fused<D, S, real, TX, TY, MINB, false, CL>;
+      auto kern = l.small ? k_step_fused<D, S, real, TX, TY, MINB, true, CL, OPT & ~kOptRows>
+                          : (l.rows ? k_step_fused<D, S, real, TX, TY, MINB, false, CL, OPT>
+                                    : k_step_fused<D, S, real, TX, TY, MINB, false, CL, OPT & ~kOptRows>);
       kern<<<l.grid, FG::NT, smem(), h.stream>>>(p, reinterpret_cast<const ST*>(src), reinterpret_cast<ST*>(dst),
                                                  h.err_dev, l.ncolx, l.ncoly, l.nseg);
       h.launches += 1;
@@ -117,7 +122,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   // so its list also offers the unrestricted (MINB 1) allocation.
   template <class CL> static int candidates(const LaunchFn** fns) {
     if constexpr (CL::kPr) {                                   // one shape: the Peng-Robinson sets compile fast
-      static const LaunchFn c[] = {D == 3 ? &Fused<32, 8, sizeof(real) == 8 ? 1 : 2, CL>::launch
+      static const LaunchFn c[] = {D == 3 ? &Fused<32, 8, sizeof(real) == 8 ? 1 : 2, CL, kOptRows>::launch
                                           : &Fused<256, 1, 2, CL>::launch};
       *fns = c;
       return 1;
@@ -128,12 +133,12 @@ template <int D, typename S, typename real> struct OpsImpl {
         return 1;
       } else if constexpr (CL::kWarp) {
         static const LaunchFn c[] = {&Fused<32, 8, 2, CL>::launch, &Fused<32, 8, 1, CL>::launch,
-                                     &Fused<32, 16, 1, CL>::launch};
+                                     &Fused<32, 16, 1, CL>::launch, &Fused<32, 8, 1, CL, kOptRows>::launch};
         *fns = c;
-        return 3;
+        return 4;
       } else {
-        static const LaunchFn c[] = {&Fused<32, 8, 2, CL>::launch, &Fused<32, 16, 1, CL>::launch,
-                                     &Fused<16, 16, 2, CL>::launch};
+        static const LaunchFn c[] = {&Fused<32, 8, 2, CL, kOptRows>::launch, &Fused<32, 16, 1, CL, kOptRows>::launch,
+                                     &Fused<16, 16, 2, CL, kOptRows>::launch};
         *fns = c;
         return 3;
       }

@@ -355,6 +355,8 @@ TILE_CASES = [
     ("d2 riemann 300x7 fp64", lambda: inputs.add_noise(inputs.riemann(Nx=300, Ny=7), 2), "fp64"),
     ("d2 couette walls 600x3 fp32", lambda: inputs.couette(2, (600, 3), Ma=0.5, seed=3, rel=1e-2), "fp32"),
     ("d3 tgv 40x27x18 fp32", lambda: tgv_case((40, 27, 18)), "fp32"),
+    ("d3 tgv 40x27x18 fp16dev", lambda: tgv_case((40, 27, 18)), "fp16dev"),
+    ("d3 tgv 44x23x9 fp32", lambda: tgv_case((44, 23, 9)), "fp32"),
 ]
 
 
