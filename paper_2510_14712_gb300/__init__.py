@@ -332,11 +332,11 @@ def lbm_set_tile(h, index):
 
 def lbm_autotune_times(h):
     """ms per step of every tile candidate at the last lbm_autotune."""
-    ms = np.zeros(8, dtype=np.float32)
-    n = load().lbm_autotune_times(h, ms.ctypes.data_as(ctypes.c_void_p), 8)
+    ms = np.zeros(16, dtype=np.float32)
+    n = load().lbm_autotune_times(h, ms.ctypes.data_as(ctypes.c_void_p), 16)
     if n < 0:
         _check(n)
-    return ms[:n].tolist()
+    return ms[:min(n, 16)].tolist()
 
 
 def lbm_launch_count(h):

@@ -21,7 +21,9 @@
 //      populations again (they were read three planes earlier: L2 hits).
 // The 3-plane lag is the z-extent of the dependency cone: the collision at z
 // needs u at z+-1, which needs F at z+-1, which needs lap rho at z+-2, which
-// needs rho at z+-3.
+// needs rho at z+-3.  With kOptPair each stage handles two planes between its
+// barriers (A: pl, pl+1; B: pl-1, pl; C: pl-2, pl-1; D: pl-3, pl-2), halving
+// the barriers per node; the rings then hold four planes.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -31,8 +33,12 @@ namespace lbm {
 
 // EX: extra per-node fields of the primitive ring (2 when the closure's P and
 // c_s^2 are stored for the collision instead of recomputed there).
-template <int D, int TX, int TY, int EX = 0> struct FusedGeom {
+// NP: planes per barrier interval (each stage handles NP planes between two
+// barriers); the rings then hold R = NP + 2 planes and the centre ring CN =
+// NP + 1.
+template <int D, int TX, int TY, int EX = 0, int NP = 1> struct FusedGeom {
   static constexpr int NT = TX * TY;                 // threads per CTA
+  static constexpr int R = NP + 2, CN = NP + 1;
   static constexpr int HY3 = D == 3 ? 3 : 0, HY2 = D == 3 ? 2 : 0, HY1 = D == 3 ? 1 : 0;
   static constexpr int BX3 = TX + 6, BY3 = TY + 2 * HY3, N3 = BX3 * BY3;
   static constexpr int BX2 = TX + 4, BY2 = TY + 2 * HY2, N2 = BX2 * BY2;
@@ -41,15 +47,15 @@ template <int D, int TX, int TY, int EX = 0> struct FusedGeom {
   // primitive ring on R1 (read at the node and its neighbours): u[D], T, h, Lam[D]
   static constexpr int NPRIM = 2 * D + 2;
   static constexpr int P_U = 0, P_T = D, P_H = D + 1, P_LAM = D + 2;
-  // centre ring on the tile only (read at the node): rho, F[D] (, P, c_s^2), two planes
+  // centre ring on the tile only (read at the node): rho, F[D] (, P, c_s^2), CN planes
   static constexpr int NCEN = 1 + D + EX;
   static constexpr int C_RHO = 0, C_F = 1, C_P = 1 + D, C_CS2 = 2 + D;
   // own density of the two R1 ghost columns next to wall faces (x = -1, Nx),
-  // three planes: the density ring holds their mirror images instead
-  static constexpr int NGOWN = 3 * 2 * BY1;
+  // R planes: the density ring holds their mirror images instead
+  static constexpr int NGOWN = R * 2 * BY1;
   // bytes of the rings, rounded up to 16 (a closure's table follows them)
   template <typename real> static constexpr size_t smem_bytes() {
-    return (sizeof(real) * size_t(3 * N3 + 3 * NMOM * N1 + 3 * N2 + 3 * NPRIM * N1 + 2 * NCEN * NT + NGOWN) + 15) &
+    return (sizeof(real) * size_t(R * N3 + R * NMOM * N1 + R * N2 + R * NPRIM * N1 + CN * NCEN * NT + NGOWN) + 15) &
            ~size_t(15);
   }
 };
@@ -169,7 +175,9 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
 //     in the same order as the position form, so both give the same bits.
 //     Stage D's in-plane pull offsets are computed once per work item (the
 //     thread's node is the same on every plane).
-constexpr int kOptRows = 1;
+//   kOptPair: two planes per barrier interval (stages A to D each handle two
+//     planes between their barriers; rings of four planes).
+constexpr int kOptRows = 1, kOptPair = 2;
 
 // One (column, z-segment) work item of the fused step: all planes mb..me-1 of
 // the column of TX x hy nodes at (x0, y0) (hy <= TY rows; 1 in 2-D), reading A
@@ -182,14 +190,18 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
                                              typename Store<S>::T* __restrict__ B, int x0, int y0, int hy, int mb,
                                              int me, unsigned char* smem_raw, unsigned& flags, const CL& closure) {
   using L = Lattice<D>;
-  using G = FusedGeom<D, TX, TY, CL::kExtra>;
+  constexpr int NP = (OPT & kOptPair) ? 2 : 1;
+  using G = FusedGeom<D, TX, TY, CL::kExtra, NP>;
   constexpr int Q = L::Q;
-  real* s_rho = reinterpret_cast<real*>(smem_raw);            // [3][N3]
-  real* s_mom = s_rho + 3 * G::N3;                            // [3][NMOM][N1]
-  real* s_lap = s_mom + 3 * G::NMOM * G::N1;                  // [3][N2]
-  real* s_prm = s_lap + 3 * G::N2;                            // [3][NPRIM][N1]
-  real* s_cen = s_prm + 3 * G::NPRIM * G::N1;                 // [2][NCEN][NT]
-  real* s_gown = s_cen + 2 * G::NCEN * G::NT;                 // [3][2][BY1]
+  real* s_rho = reinterpret_cast<real*>(smem_raw);            // [R][N3]
+  real* s_mom = s_rho + G::R * G::N3;                         // [R][NMOM][N1]
+  real* s_lap = s_mom + G::R * G::NMOM * G::N1;               // [R][N2]
+  real* s_prm = s_lap + G::R * G::N2;                         // [R][NPRIM][N1]
+  real* s_cen = s_prm + G::R * G::NPRIM * G::N1;              // [CN][NCEN][NT]
+  real* s_gown = s_cen + G::CN * G::NCEN * G::NT;             // [R][2][BY1]
+  // ring slot of plane v >= -4
+  auto rs = [](int v) { return (v + 4 * G::R) % G::R; };
+  auto cs = [](int v) { return (v + 4 * G::CN) % G::CN; };
 
   const Model<real> m = model_of<real>(p);
   const int tid = threadIdx.x;
@@ -215,16 +227,11 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     }
   }
 
-  for (int pl = mb - 3; pl <= me + 2; ++pl) {
-    // ---------------- A: moments of plane pl --------------------------------
+  for (int pl = mb - 3; pl <= me + 2; pl += NP) {
+    // ---------------- A: moments of planes pl .. pl+NP-1 ----------------------
     if constexpr (kRows) {
       constexpr int NCH = (TX + 8) / 4, RPW = 32 / NCH;
       static_assert(TX % 4 == 0 && RPW >= 1, "row form: TX + 8 nodes in 4-node chunks, at least one row per warp");
-      const int slot = (pl + 6) % 3;
-      const int mp = modp(pl, Nm);
-      const ST* Pm[3];
-#pragma unroll
-      for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
       const int lane = tid & 31, rr = lane / NCH, ch = lane - rr * NCH;
       // Row groups of three kinds: f rows of the R1 box (rho and j), g rows of
       // the R1 box (S), and the four f rows of the R3 box outside it (rho
@@ -237,8 +244,16 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       xs += xs < 0 ? p.Nx : 0;
       xs -= xs >= p.Nx ? p.Nx : 0;
       for (int k = 0;; ++k) {
-        const int gi = (k & 1) ? (k + 1) * nw - 1 - w : k * nw + w;
-        if (gi >= ngroups) break;
+        // group index over the NP planes of the interval
+        const int gp = (k & 1) ? (k + 1) * nw - 1 - w : k * nw + w;
+        if (gp >= NP * ngroups) break;
+        const int pa = pl + gp / ngroups, gi = gp % ngroups;
+        if (pa > me + 2) continue;                                      // warp-uniform
+        const int slot = rs(pa);
+        const int mp = modp(pa, Nm);
+        const ST* Pm[3];
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
         const int kind = gi < g1 ? 0 : (gi < 2 * g1 ? 1 : 2);          // warp-uniform
         const int r = (gi - (kind == 0 ? 0 : (kind == 1 ? g1 : 2 * g1))) * RPW + rr;
         const bool act = rr < RPW && r < (kind == 2 ? 4 : n1);
@@ -347,9 +362,11 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     // populations and j is then exactly zero (as the pairwise sum of Eq.
     // def_u).  Positions 0 .. KFULL*NT-1 are spread over all threads; the
     // remainder (fewer than NT) is done by the first threads only.
-    {
-      const int slot = (pl + 6) % 3;
-      const int mp = modp(pl, Nm);
+    for (int sa = 0; sa < NP; ++sa) {
+      const int pa = pl + sa;
+      if (pa > me + 2) break;
+      const int slot = rs(pa);
+      const int mp = modp(pa, Nm);
       const ST* Pm[3];
 #pragma unroll
       for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
@@ -419,10 +436,11 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     }
     __syncthreads();
 
-    // ---------------- B: Laplacian of rho, plane pl-1, on R2 ------------------
-    if (pl - 1 >= mb - 2) {
-      const int q = pl - 1;
-      const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
+    // ---------------- B: Laplacian of rho, planes pl-1 .., on R2 --------------
+    for (int sq = 0; sq < NP; ++sq) {
+      const int q = pl - 1 + sq;
+      if (q < mb - 2 || q > me + 1) continue;
+      const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       for (int k = tid; k < G::N2; k += G::NT) {
         const int lx = k % G::BX2, ly = k / G::BX2;
         const int ox = outside(lx, 2, TX), oy = D == 3 ? outside(ly, G::HY2, hy) : 0;
@@ -439,12 +457,13 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     }
     __syncthreads();
 
-    // ---------------- C: primitive fields, plane pl-2, on R1 ------------------
+    // ---------------- C: primitive fields, planes pl-2 .., on R1 --------------
     // The loop runs a warp-uniform number of times (warp-collective closures);
     // `act` marks the lanes whose position is a needed node.
-    if (pl - 2 >= mb - 1) {
-      const int q = pl - 2;
-      const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
+    for (int sq = 0; sq < NP; ++sq) {
+      const int q = pl - 2 + sq;
+      if (q < mb - 1 || q > me) continue;
+      const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       const int lane = tid & 31;
       for (int k0 = tid - lane; k0 < G::N1; k0 += G::NT) {
         const int k = k0 + lane;
@@ -503,7 +522,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
                 W[(1 + D) * p.plane + o] = T;
               }
             }
-            real* ce = s_cen + ((q & 1) * G::NCEN) * G::NT + (ly - G::HY1) * TX + (lx - 1);
+            real* ce = s_cen + (cs(q) * G::NCEN) * G::NT + (ly - G::HY1) * TX + (lx - 1);
             ce[G::C_RHO * G::NT] = rho;
 #pragma unroll
             for (int a = 0; a < D; ++a) ce[(G::C_F + a) * G::NT] = F[a];
@@ -517,10 +536,11 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     }
     __syncthreads();
 
-    // ---------------- D: collide plane pl-3 on the tile --------------------------
-    if (pl - 3 >= mb) {
-      const int q = pl - 3;
-      const int sc = (q + 6) % 3, sm = (q + 5) % 3, sp = (q + 7) % 3;
+    // ---------------- D: collide planes pl-3 .. on the tile ----------------------
+    for (int sq = 0; sq < NP; ++sq) {
+      const int q = pl - 3 + sq;
+      if (q < mb || q >= me) continue;
+      const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       const int lx = tid % TX, ly = tid / TX;
       const int gx = x0 + lx, gy = y0 + ly;
       if (gx < p.Nx && (D == 2 || (ly < hy && gy < p.Ny))) {
@@ -544,7 +564,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
         const real* pm = s_prm + (sm * G::NPRIM) * G::N1;
         const real* pp = s_prm + (sp * G::NPRIM) * G::N1;
         NodeState<D, real> s;
-        const real* cc = s_cen + ((q & 1) * G::NCEN) * G::NT + tid;
+        const real* cc = s_cen + (cs(q) * G::NCEN) * G::NT + tid;
         s.rho = cc[G::C_RHO * G::NT];
         s.T = pc[G::P_T * G::N1 + k1];
         if constexpr (CL::kExtra > 0) {
@@ -636,7 +656,7 @@ k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __res
              typename Store<S>::T* __restrict__ B, unsigned* err, int ncolx, int ncoly, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CL closure;
-  closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra>::template smem_bytes<real>());
+  closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra, (OPT & kOptPair) ? 2 : 1>::template smem_bytes<real>());
   if constexpr (CL::kSmem > 0) __syncthreads();
   unsigned flags = 0;
   const int Nm = D == 3 ? p.Nz : p.Ny;

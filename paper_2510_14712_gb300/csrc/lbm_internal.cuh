@@ -15,6 +15,7 @@ namespace lbm {
 
 constexpr int kGhost = 4;         // ghost layers per non-periodic x face
 constexpr int kMaxPartials = 1024;
+constexpr int kMaxTiles = 16;     // tile candidates whose autotune times are kept
 
 // Everything a kernel needs, passed by value.
 struct Params {
@@ -98,7 +99,7 @@ struct Handle {
   long long launches;
   int closure;                // LBM_CLOSURE_EXACT | LBM_CLOSURE_MLP
   void* mlp_img;              // device copy of the attached network's inference image
-  float tune_ms[8];           // ms per step of every candidate at the last lbm_autotune
+  float tune_ms[kMaxTiles];    // ms per step of every candidate at the last lbm_autotune
   int tune_n;
   int use_graphs;             // lbm_set_graphs: replay captured two-step graphs
   void* graphs;               // StepGraphs (lbm_capi.cu), created on first use

@@ -43,7 +43,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   // One tile shape of the fused kernel (TX x TY in-plane nodes, MINB CTAs
   // per SM for the register budget) with thermodynamic closure CL.
   template <int TX, int TY, int MINB, class CL, int OPT = 0> struct Fused {
-    using FG = FusedGeom<D, TX, TY, CL::kExtra>;
+    using FG = FusedGeom<D, TX, TY, CL::kExtra, (OPT & kOptPair) ? 2 : 1>;
     static size_t smem() { return FG::template smem_bytes<real>() + CL::kSmem; }
     struct Launch {
       int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
@@ -138,9 +138,11 @@ template <int D, typename S, typename real> struct OpsImpl {
         return 4;
       } else {
         static const LaunchFn c[] = {&Fused<32, 8, 2, CL, kOptRows>::launch, &Fused<32, 16, 1, CL, kOptRows>::launch,
-                                     &Fused<16, 16, 2, CL, kOptRows>::launch};
+                                     &Fused<16, 16, 2, CL, kOptRows>::launch,
+                                     &Fused<32, 8, 2, CL, kOptRows | kOptPair>::launch,
+                                     &Fused<32, 16, 1, CL, kOptRows | kOptPair>::launch};
         *fns = c;
-        return 3;
+        return 5;
       }
     } else if constexpr (sizeof(real) == 4 && !CL::kWarp) {
       // narrow tiles spread small domains (few columns) over more SMs; the
@@ -150,9 +152,10 @@ template <int D, typename S, typename real> struct OpsImpl {
       static const LaunchFn c[] = {&Fused<256, 1, 2, CL>::launch, &Fused<128, 1, 4, CL>::launch,
                                    &Fused<512, 1, 1, CL>::launch, &Fused<64, 1, 8, CL>::launch,
                                    &Fused<32, 1, 16, CL>::launch, &Fused<256, 1, 3, CL>::launch,
-                                   &Fused<128, 1, 6, CL>::launch};
+                                   &Fused<128, 1, 6, CL>::launch, &Fused<128, 1, 6, CL, kOptPair>::launch,
+                                   &Fused<256, 1, 3, CL, kOptPair>::launch};
       *fns = c;
-      return 7;
+      return 9;
     } else {
       static const LaunchFn c[] = {&Fused<256, 1, 2, CL>::launch, &Fused<128, 1, 4, CL>::launch,
                                    &Fused<512, 1, 1, CL>::launch, &Fused<64, 1, 8, CL>::launch,
@@ -208,7 +211,7 @@ template <int D, typename S, typename real> struct OpsImpl {
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (c < 8) h.tune_ms[c] = ms / (reps > 0 ? reps : 1);
+      if (c < kMaxTiles) h.tune_ms[c] = ms / (reps > 0 ? reps : 1);
       if (ms < bt) {
         bt = ms;
         best = c;
@@ -217,7 +220,7 @@ template <int D, typename S, typename real> struct OpsImpl {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h.tile_cfg = best;
-    h.tune_n = n < 8 ? n : 8;
+    h.tune_n = n < kMaxTiles ? n : kMaxTiles;
     if (best_ms) *best_ms = bt / (reps > 0 ? reps : 1);
     return best;
   }
