@@ -162,13 +162,14 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
 }
 
 // Options of the fused step (template bit mask).
-//   kOptRows: stage A in row form (3-D; FP32 or FP16-deviation storage; x
-//     periodic with Nx a multiple of 4; not SMALL): the R3 box is cut into
+//   kOptRows: stage A in row form (3-D; FP32 or FP16-deviation storage; Nx a
+//     multiple of 4; not SMALL; no wall face, whose ghost columns take mirror
+//     densities in the position form): the R3 box is cut into
 //     rows of TX + 8 nodes that start 4 nodes left of the tile, and each row
 //     into chunks of 4 nodes, one chunk per lane.  A lane reads the 4 values of
 //     one direction with one 16-byte (FP16: 8-byte) load of the source row
-//     (aligned: x0 and Nx are multiples of 4, so a chunk never straddles the
-//     periodic seam), and the value a node pulls from across the chunk edge
+//     (aligned: x0, Nx and the ghost width are multiples of 4, so a chunk
+//     never straddles the periodic seam), and the value a node pulls from across the chunk edge
 //     comes from the neighbouring lane by a shuffle.  Warps take groups of
 //     whole rows: the f rows of the R3 box (rho; j on the R1 rows), then the
 //     g rows of the R1 box (S).  Per node and direction the moments are summed
@@ -240,9 +241,17 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       const int n1 = hy + 2 * G::HY1;                                   // rows of the R1 box
       const int g1 = (n1 + RPW - 1) / RPW, g3 = (4 + RPW - 1) / RPW;
       const int ngroups = 2 * g1 + g3, nw = G::NT / 32, w = tid >> 5;
-      int xs = x0 - 4 + 4 * ch;                                         // first node of the chunk
-      xs += xs < 0 ? p.Nx : 0;
-      xs -= xs >= p.Nx ? p.Nx : 0;
+      // padded x of the chunk's first node: wrapped when x is periodic; else
+      // shifted by the ghost layers, and chunks past the last one a node of
+      // the box pulls from (x = Nx + 3, inside the row since Nx and G are
+      // multiples of 4) are moved into the row (their values are not used)
+      int xs = x0 - 4 + 4 * ch;
+      if (p.periodic_x) {
+        xs += xs < 0 ? p.Nx : 0;
+        xs -= xs >= p.Nx ? p.Nx : 0;
+      } else {
+        xs = min(xs + p.G, p.pitch - 4);
+      }
       for (int k = 0;; ++k) {
         // group index over the NP planes of the interval
         const int gp = (k & 1) ? (k + 1) * nw - 1 - w : k * nw + w;

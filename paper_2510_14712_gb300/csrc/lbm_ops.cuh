@@ -99,8 +99,10 @@ template <int D, typename S, typename real> struct OpsImpl {
       if (g > slots) g = slots;
       l.grid = int(g);
       l.small = (p.periodic_x && p.Nx < TX + 6) || (D == 3 && p.Ny < TY + 6);
-      // row form of stage A: aligned 4-node chunks of periodic rows
-      l.rows = (OPT & kOptRows) && D == 3 && sizeof(real) == 4 && !l.small && p.periodic_x && p.Nx % 4 == 0;
+      // row form of stage A: aligned 4-node chunks (Nx and the ghost width are
+      // multiples of 4), no wall face (mirror densities in stage A)
+      l.rows = (OPT & kOptRows) && D == 3 && sizeof(real) == 4 && !l.small && p.Nx % 4 == 0 && p.G % 4 == 0 &&
+               p.bc_lo != LBM_BC_WALL && p.bc_hi != LBM_BC_WALL;
       return l;
     }
     static void launch(Handle& h, const void* src, void* dst) {

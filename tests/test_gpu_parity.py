@@ -226,6 +226,19 @@ def test_shock_tube(precision):
     assert_parity(got, want, tol, "shock tube " + precision)
 
 
+def shock_tube_3d():
+    """D3Q27 Ma 1.2 shock tube with inflow / outflow x faces, Nx a multiple of 4
+    and Ny >= 14: the default tile reads stage A in row form with ghost columns."""
+    import mlp_util
+    return mlp_util.shock_tube(3, (96, 16, 6))
+
+
+def test_shock_tube_3d_fp32():
+    want = oracle_run(shock_tube_3d(), 60)
+    got = gpu_run(shock_tube_3d(), 60, "fp32")
+    assert_parity(got, want, fp32_bound_of(shock_tube_3d(), 60, want), "3-D shock tube fp32")
+
+
 # ---- edge cases --------------------------------------------------------------------
 
 @pytest.mark.parametrize("shape", [(5, 1), (1, 6), (3, 2)])
@@ -357,6 +370,8 @@ TILE_CASES = [
     ("d3 tgv 40x27x18 fp32", lambda: tgv_case((40, 27, 18)), "fp32"),
     ("d3 tgv 40x27x18 fp16dev", lambda: tgv_case((40, 27, 18)), "fp16dev"),
     ("d3 tgv 44x23x9 fp32", lambda: tgv_case((44, 23, 9)), "fp32"),
+    ("d3 shock tube 96x16x6 fp32", lambda: shock_tube_3d(), "fp32"),
+    ("d3 couette walls 76x16x5 fp32", lambda: inputs.couette(3, (76, 16, 5), Ma=0.5, seed=5, rel=1e-3), "fp32"),
 ]
 
 
