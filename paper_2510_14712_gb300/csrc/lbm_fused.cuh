@@ -180,6 +180,9 @@ __device__ __forceinline__ int outside(int l, int h, int T) {
 //     planes between their barriers; rings of four planes).
 constexpr int kOptRows = 1, kOptPair = 2;
 
+// planes per barrier interval of option set OPT
+template <int OPT> constexpr int planes_per_interval() { return (OPT & kOptPair) ? 2 : 1; }
+
 // One (column, z-segment) work item of the fused step: all planes mb..me-1 of
 // the column of TX x hy nodes at (x0, y0) (hy <= TY rows; 1 in 2-D), reading A
 // and writing B.  Shared by the single-instance kernel and the batched
@@ -191,7 +194,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
                                              typename Store<S>::T* __restrict__ B, int x0, int y0, int hy, int mb,
                                              int me, unsigned char* smem_raw, unsigned& flags, const CL& closure) {
   using L = Lattice<D>;
-  constexpr int NP = (OPT & kOptPair) ? 2 : 1;
+  constexpr int NP = planes_per_interval<OPT>();
   using G = FusedGeom<D, TX, TY, CL::kExtra, NP>;
   constexpr int Q = L::Q;
   real* s_rho = reinterpret_cast<real*>(smem_raw);            // [R][N3]
@@ -201,8 +204,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
   real* s_cen = s_prm + G::R * G::NPRIM * G::N1;              // [CN][NCEN][NT]
   real* s_gown = s_cen + G::CN * G::NCEN * G::NT;             // [R][2][BY1]
   // ring slot of plane v >= -4
-  auto rs = [](int v) { return (v + 4 * G::R) % G::R; };
-  auto cs = [](int v) { return (v + 4 * G::CN) % G::CN; };
+  auto rs = [](int v) { return G::R == 3 ? (v + 6) % 3 : (v + 8) & 3; };
+  auto cs = [](int v) { return G::CN == 2 ? (v & 1) : (v + 6) % 3; };
 
   const Model<real> m = model_of<real>(p);
   const int tid = threadIdx.x;
@@ -233,6 +236,21 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     if constexpr (kRows) {
       constexpr int NCH = (TX + 8) / 4, RPW = 32 / NCH;
       static_assert(TX % 4 == 0 && RPW >= 1, "row form: TX + 8 nodes in 4-node chunks, at least one row per warp");
+      // plane pointers and ring slots of the interval's planes (NP <= 2)
+      const ST* PmA[3];
+      const ST* PmB[3];
+      int slotA = rs(pl), slotB = slotA;
+      {
+        const int mp = modp(pl, Nm);
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) PmA[c + 1] = PmB[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
+      }
+      if constexpr (NP > 1) {
+        const int mp = modp(pl + 1, Nm);
+        slotB = rs(pl + 1);
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) PmB[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
+      }
       const int lane = tid & 31, rr = lane / NCH, ch = lane - rr * NCH;
       // Row groups of three kinds: f rows of the R1 box (rho and j), g rows of
       // the R1 box (S), and the four f rows of the R3 box outside it (rho
@@ -256,13 +274,12 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
         // group index over the NP planes of the interval
         const int gp = (k & 1) ? (k + 1) * nw - 1 - w : k * nw + w;
         if (gp >= NP * ngroups) break;
-        const int pa = pl + gp / ngroups, gi = gp % ngroups;
-        if (pa > me + 2) continue;                                      // warp-uniform
-        const int slot = rs(pa);
-        const int mp = modp(pa, Nm);
-        const ST* Pm[3];
-#pragma unroll
-        for (int c = -1; c <= 1; ++c) Pm[c + 1] = A + (long long)wrap(mp - c, Nm) * mstride;
+        static_assert(NP == 1 || NP == 2, "one or two planes per interval");
+        const int sa = NP == 1 ? 0 : int(gp >= ngroups);
+        const int pa = pl + sa, gi = gp - sa * ngroups;
+        if (NP > 1 && pa > me + 2) continue;                            // warp-uniform
+        const int slot = sa ? slotB : slotA;
+        const ST* Pm[3] = {sa ? PmB[0] : PmA[0], sa ? PmB[1] : PmA[1], sa ? PmB[2] : PmA[2]};
         const int kind = gi < g1 ? 0 : (gi < 2 * g1 ? 1 : 2);          // warp-uniform
         const int r = (gi - (kind == 0 ? 0 : (kind == 1 ? g1 : 2 * g1))) * RPW + rr;
         const bool act = rr < RPW && r < (kind == 2 ? 4 : n1);
@@ -373,7 +390,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     // remainder (fewer than NT) is done by the first threads only.
     for (int sa = 0; sa < NP; ++sa) {
       const int pa = pl + sa;
-      if (pa > me + 2) break;
+      if (NP > 1 && pa > me + 2) break;
       const int slot = rs(pa);
       const int mp = modp(pa, Nm);
       const ST* Pm[3];
@@ -448,7 +465,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     // ---------------- B: Laplacian of rho, planes pl-1 .., on R2 --------------
     for (int sq = 0; sq < NP; ++sq) {
       const int q = pl - 1 + sq;
-      if (q < mb - 2 || q > me + 1) continue;
+      if (q < mb - 2 || (NP > 1 && q > me + 1)) continue;
       const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       for (int k = tid; k < G::N2; k += G::NT) {
         const int lx = k % G::BX2, ly = k / G::BX2;
@@ -471,7 +488,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     // `act` marks the lanes whose position is a needed node.
     for (int sq = 0; sq < NP; ++sq) {
       const int q = pl - 2 + sq;
-      if (q < mb - 1 || q > me) continue;
+      if (q < mb - 1 || (NP > 1 && q > me)) continue;
       const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       const int lane = tid & 31;
       for (int k0 = tid - lane; k0 < G::N1; k0 += G::NT) {
@@ -548,7 +565,7 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
     // ---------------- D: collide planes pl-3 .. on the tile ----------------------
     for (int sq = 0; sq < NP; ++sq) {
       const int q = pl - 3 + sq;
-      if (q < mb || q >= me) continue;
+      if (q < mb || (NP > 1 && q >= me)) continue;
       const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       const int lx = tid % TX, ly = tid / TX;
       const int gx = x0 + lx, gy = y0 + ly;
@@ -665,7 +682,7 @@ k_step_fused(const __grid_constant__ Params p, const typename Store<S>::T* __res
              typename Store<S>::T* __restrict__ B, unsigned* err, int ncolx, int ncoly, int nseg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CL closure;
-  closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra, (OPT & kOptPair) ? 2 : 1>::template smem_bytes<real>());
+  closure.load(p, smem_raw + FusedGeom<D, TX, TY, CL::kExtra, planes_per_interval<OPT>()>::template smem_bytes<real>());
   if constexpr (CL::kSmem > 0) __syncthreads();
   unsigned flags = 0;
   const int Nm = D == 3 ? p.Nz : p.Ny;

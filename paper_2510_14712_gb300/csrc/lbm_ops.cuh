@@ -43,7 +43,7 @@ template <int D, typename S, typename real> struct OpsImpl {
   // One tile shape of the fused kernel (TX x TY in-plane nodes, MINB CTAs
   // per SM for the register budget) with thermodynamic closure CL.
   template <int TX, int TY, int MINB, class CL, int OPT = 0> struct Fused {
-    using FG = FusedGeom<D, TX, TY, CL::kExtra, (OPT & kOptPair) ? 2 : 1>;
+    using FG = FusedGeom<D, TX, TY, CL::kExtra, planes_per_interval<OPT>()>;
     static size_t smem() { return FG::template smem_bytes<real>() + CL::kSmem; }
     struct Launch {
       int grid = 0, ncolx = 0, ncoly = 0, nseg = 1;
