@@ -467,7 +467,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       const int q = pl - 1 + sq;
       if (q < mb - 2 || (NP > 1 && q > me + 1)) continue;
       const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
-      for (int k = tid; k < G::N2; k += G::NT) {
+      const int n2 = G::BX2 * (hy + 2 * G::HY2);              // the band's rows of the R2 box
+      for (int k = tid; k < n2; k += G::NT) {
         const int lx = k % G::BX2, ly = k / G::BX2;
         const int ox = outside(lx, 2, TX), oy = D == 3 ? outside(ly, G::HY2, hy) : 0;
         if (ox + oy > 2) continue;
@@ -491,7 +492,8 @@ __device__ __forceinline__ void fused_column(const Params& p, const typename Sto
       if (q < mb - 1 || (NP > 1 && q > me)) continue;
       const int sc = rs(q), sm = rs(q - 1), sp = rs(q + 1);
       const int lane = tid & 31;
-      for (int k0 = tid - lane; k0 < G::N1; k0 += G::NT) {
+      const int n1 = G::BX1 * (hy + 2 * G::HY1);              // the band's rows of the R1 box
+      for (int k0 = tid - lane; k0 < n1; k0 += G::NT) {
         const int k = k0 + lane;
         const int lx = k % G::BX1, ly = k / G::BX1;
         const int ox = outside(lx, 1, TX), oy = D == 3 ? outside(ly, G::HY1, hy) : 0;
