@@ -152,6 +152,39 @@ def gpu_mlp_run(P, case, steps, theta, scale, chunk=None):
         net.close()
 
 
+def test_mlp_every_tile_shape_gives_the_same_step(P, onet):
+    """The learned closure's tile candidates (position-form stage A, row form on
+    inflow / outflow faces) step a D3Q27 shock tube alike."""
+    theta, scale = onet
+    case = mlp_util.shock_tube(3, (96, 16, 6))
+    net = make_net(P)
+    net.params = theta
+    net.scaling = scale
+    s = P.Solver(case, precision="fp32")
+    try:
+        ref = None
+        n = None
+        for k in range(16):
+            s.init()
+            net.attach(s)
+            if n is None:
+                n = P.lbm_tile_count(s.h)
+                assert n >= 2
+            if k >= n:
+                break
+            P.lbm_set_tile(s.h, k)
+            s.step(12)
+            got = s.fields()
+            if ref is None:
+                ref = got
+                continue
+            for key in ("rho", "u", "T"):
+                assert rel_l2(got[key], ref[key]) < 1e-6, "tile %d of %d: %s" % (k, n, key)
+    finally:
+        s.close()
+        net.close()
+
+
 @pytest.mark.parametrize("D,shape,steps", [(2, (256, 4), 300), (2, (197, 3), 120), (3, (72, 6, 5), 40)])
 def test_mlp_step_matches_oracle(P, onet, D, shape, steps):
     theta, scale = onet
