@@ -218,16 +218,22 @@ __host__ __device__ inline void equilibria(const Model<real>& m, real rho, const
   const real theta = P / rho;
   const real e = eos_energy(m, rho, T);
   Axis3<real> ps[D], ch[D];
+#pragma unroll
   for (int a = 0; a < D; ++a) {
     ps[a] = psi3(u[a], theta + u[a] * u[a]);
     ch[a] = chi3(u[a], theta);
   }
+  // unrolled: table indices are compile-time, the tables stay in registers
+#pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     real prod = real(1);
+#pragma unroll
     for (int a = 0; a < D; ++a) prod *= ps[a][L::c(i, a)];
     real acc = e * prod;
+#pragma unroll
     for (int b = 0; b < D; ++b) {
       real t = ch[b][L::c(i, b)];
+#pragma unroll
       for (int a = 0; a < D; ++a)
         if (a != b) t *= ps[a][L::c(i, a)];
       acc += t;

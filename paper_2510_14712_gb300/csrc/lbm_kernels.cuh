@@ -178,8 +178,11 @@ __device__ inline void prim_ext(const Params& p, const double* rho, const double
 // Thread per source node x in [-G-1, Nx+G] (bounded) or [0, Nx) (periodic);
 // writes A_i(x - c_i) = eq_i(x), which is what node x - c_i + c_i = x pulls.
 // ---------------------------------------------------------------------------
+// (Params as a grid constant: prim_ext takes the address of its inflow state,
+// which would otherwise copy the whole parameter block to local memory)
 template <int D, typename S>
-__global__ void k_init(Params p, typename Store<S>::T* A, const double* rho, const double* u, const double* T) {
+__global__ void k_init(const __grid_constant__ Params p, typename Store<S>::T* A, const double* rho, const double* u,
+                       const double* T) {
   using L = Lattice<D>;
   const int xlo = p.periodic_x ? 0 : -p.G - 1;
   const int xhi = p.periodic_x ? p.Nx : p.Nx + p.G + 1;
@@ -191,6 +194,7 @@ __global__ void k_init(Params p, typename Store<S>::T* A, const double* rho, con
   double feq[L::Q], geq[L::Q];
   equilibria<D, double>(m, r, uu, t, feq, geq);
   const int NxP = p.Nx + 2 * p.G;
+#pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     int xs = x - L::c(i, 0) + p.G;
     if (p.periodic_x) xs = wrap(xs, p.Nx);
